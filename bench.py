@@ -1,0 +1,404 @@
+#!/usr/bin/env python
+"""Benchmark of the non-Hermitian FEAST hot path on one GB300 per rank.
+
+Workload: 2D convection-diffusion, 5-point upwind finite differences on a
+300 x 300 grid (n = 90 000, 448 800 nonzeros, Peclet 10), B = I, an ellipse
+(axis ratio 0.5) around 30 interior eigenvalues, m0 = 64, ne = 16 trapezoid
+nodes, seeded N(0,1) start blocks.  One step = one full solve (factorisation
+of the 16 shifted matrices, contour integrations, Rayleigh-Ritz, convergence
+test, output) from the same start blocks; the metric is converged eigenpairs
+(eq. res <= 1e-10) per second.
+
+--impl reference times the CPU oracle (the plain FP64 algorithm, scipy
+SuperLU per node) on a bounded sample of the same workload and extrapolates
+to one full solve.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "eigenpairs/s at residual <=1e-10 (chosen vs plain FP64 form); SpMM HBM GB/s"
+UNIT = "eigenpairs/s"
+WORKLOAD = ("convdiff2d N=300 (n=90000, nnz=448800), Pe=10 upwind, B=I, ellipse ratio 0.5 around 30 "
+            "eigenvalues, m0=64, ne=16")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--form", choices=["chosen", "plain"], default="chosen")
+    p.add_argument("--N", type=int, default=300)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison solve")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def rank_info():
+    r = int(os.environ.get("RANK", "0"))
+    w = int(os.environ.get("WORLD_SIZE", "1"))
+    lr = int(os.environ.get("LOCAL_RANK", "0"))
+    return r, w, lr
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.p = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1506_04463_gb300 import feast_nh as F
+    from paper_1506_04463_gb300 import workloads as wl
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    wk = wl.config2(N=args.N)
+    prec = F.PREC_FP32_IR if args.form == "chosen" else F.PREC_FP64
+    stream = torch.cuda.current_stream(dev)
+    ctx = F.FeastNH(wk.A, None, wk.contour, wk.m0, device=dev, precision=prec, timing=1)
+    Y0 = torch.from_numpy(np.ascontiguousarray(wk.Y0)).to(dev)
+    Yh0 = torch.from_numpy(np.ascontiguousarray(wk.Yh0)).to(dev)
+    # L2 flush buffer (256 MB > 129 MB L2), written between timed steps
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    for _ in range(args.warmup):
+        out = ctx.solve(Y0, Yh0)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    clk = Clocks(local_rank)
+    clk.start()
+    launches0 = F.kernel_launches()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    infos, ms_found = [], []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        out = ctx.solve(Y0, Yh0)
+        ends[k].record(stream)
+        infos.append(out["info"])
+        ms_found.append(out["m"])
+    torch.cuda.synchronize()
+    launches = F.kernel_launches() - launches0
+    clocks = clk.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    # correctness of the timed result (closed-form spectrum of the operator)
+    lam = np.sort(out["lam"].cpu().numpy().real)
+    exact = np.sort(wk.exact.real)
+    eig_err = float(np.max(np.abs(lam - exact) / np.abs(exact))) if lam.size == exact.size else None
+    max_res = float(out["res"].max().item()) if out["m"] else None
+    pairs = sum(ms_found)
+    t = torch.tensor([total_ms, float(pairs)], dtype=torch.float64, device=dev)
+    if world > 1:
+        tt = [torch.zeros_like(t) for _ in range(world)]
+        dist.all_gather(tt, t)
+        total_max = max(float(x[0]) for x in tt)
+        pairs_all = sum(float(x[1]) for x in tt)
+    else:
+        total_max, pairs_all = total_ms, float(pairs)
+    value = pairs_all / (total_max / 1e3)
+
+    # ---- dominant kernel and its roofline ----
+    inf = infos[-1]
+    solve_ms = sum(i["t_solve_kernel_ms"] for i in infos)
+    resid_ms = sum(i["t_resid_kernel_ms"] for i in infos)
+    n_solve = sum(i["n_solve_launches"] for i in infos)
+    n_resid = sum(i["n_resid_launches"] for i in infos)
+    fac_ms = sum(i["t_factor_ms"] for i in infos)
+    n, m, ne, kl, ku = wk.A.shape[0], wk.m0, wk.contour.ne, inf["kl"], inf["ku"]
+    peaks = load_peaks()
+    sm_mhz = clocks.get("sm_max_mhz") or 2070.0
+    # one banded solve launch: both sides, every node, every column:
+    # n*(kl+ku) complex multiply-adds (8 real flops) plus n divisions, per column
+    solve_flops = 2 * ne * m * (n * (kl + ku)) * 8.0
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12       # TFLOP/s at the max SM clock
+    fp64_peak = 1.25                                          # nominal FP64 TFLOP/s of the part
+    roof = None
+    if n_solve:
+        avg = solve_ms / n_solve
+        ach = solve_flops / (avg / 1e3) / 1e12
+        peak = fp32_peak if prec == F.PREC_FP32_IR else fp64_peak
+        roof = {"kernel": "k_band_solve_ks" if prec == F.PREC_FP32_IR else "k_band_solve",
+                "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                "frac": round(ach / peak, 4), "traffic": None, "avg_launch_ms": round(avg, 3),
+                "launches": n_solve, "flops_per_launch": solve_flops,
+                "peak_note": ("FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock" if prec == F.PREC_FP32_IR
+                              else "FP64 nominal 1.25 TFLOP/s")}
+    # multi-shift residual: algorithmic bytes per launch (one side)
+    xs = ne * n * m * 16
+    resid_bytes = xs + n * m * 16 + ne * n * m * 8 + n * m * 16 + wk.A.nnz * 12 + (n + 1) * 4
+    spmm = None
+    if n_resid:
+        avg = resid_ms / n_resid
+        gbs = resid_bytes / (avg / 1e3) / 1e9
+        hbm = peaks.get("hbm_gbs", 6786.6)
+        spmm = {"kernel": "k_multishift_residual", "bound_note": "FP64 arithmetic (GB300 FP64 ~1 TFLOP/s)",
+                "achieved_gbs": round(gbs, 1), "peak_gbs": hbm, "frac_of_measured_hbm": round(gbs / hbm, 4),
+                "frac_of_8tbs": round(gbs / 8000.0, 4), "bytes_per_launch": resid_bytes,
+                "avg_launch_ms": round(avg, 3), "launches": n_resid}
+    kernel_times = {"factor_ms": round(fac_ms / len(infos), 2), "band_solve_ms": round(solve_ms / len(infos), 2),
+                    "multishift_residual_ms": round(resid_ms / len(infos), 2),
+                    "filter_ms": round(sum(i["t_filter_ms"] for i in infos) / len(infos), 2),
+                    "rr_ms": round(sum(i["t_rr_ms"] for i in infos) / len(infos), 2)}
+
+    # ---- end-to-end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_measure(args, wk, dev, prec, F, torch)
+
+    # ---- plain FP64 form, same workload, one solve ----
+    plain = None
+    if args.form == "chosen" and not args.no_plain:
+        ctxp = F.FeastNH(wk.A, None, wk.contour, wk.m0, device=dev, precision=F.PREC_FP64)
+        ctxp.solve(Y0, Yh0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        o = ctxp.solve(Y0, Yh0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1)
+        plain = {"eigenpairs_per_s": round(o["m"] / (pms / 1e3), 3), "ms_per_solve": round(pms, 1), "m": o["m"],
+                 "max_res": float(o["res"].max().item()) if o["m"] else None,
+                 "speedup_chosen_over_plain": round(value / world / (o["m"] / (pms / 1e3)), 3)}
+        ctxp.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wk, iterations=inf["iterations"])
+
+    ctx.close()
+    if rank != 0:
+        return None
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_max / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64 solves + c128 refinement/RR" if prec == F.PREC_FP32_IR else "c128",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "nnz": int(wk.A.nnz), "m0": m, "ne": ne,
+                   "form": "chosen: FP32 banded LU + FP64 iterative refinement" if prec == F.PREC_FP32_IR
+                   else "plain FP64 banded LU", "parallelism": f"replicas x{world}",
+                   "l2": "256 MB buffer written between timed steps; working set > L2"},
+        "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "spmm": spmm, "kernel_ms_per_step": kernel_times,
+        "cpu_baseline": cpu, "clocks": clocks, "plain_fp64": plain,
+        "check": {"m": int(ms_found[-1]), "iterations": inf["iterations"], "max_res": max_res,
+                  "max_rel_eig_err_vs_closed_form": eig_err},
+    }
+    return line
+
+
+def e2e_measure(args, wk, dev, prec, F, torch):
+    """Same metric through the public API with pinned host buffers: H2D of the
+    CSR matrix and start blocks, init, solve, D2H of eigenvalues, residuals and
+    both eigenvector blocks, destroy -- all inside the timed region."""
+    A = wk.A.tocsr()
+    rp = torch.from_numpy(A.indptr.astype(np.int32)).pin_memory()
+    ci = torch.from_numpy(A.indices.astype(np.int32)).pin_memory()
+    va = torch.from_numpy(A.data.real.astype(np.float64)).pin_memory()
+    Y0 = torch.from_numpy(np.ascontiguousarray(wk.Y0)).pin_memory()
+    Yh0 = torch.from_numpy(np.ascontiguousarray(wk.Yh0)).pin_memory()
+    n, m0 = A.shape[0], wk.m0
+    h_lam = torch.empty(m0, dtype=torch.complex128).pin_memory()
+    h_res = torch.empty(m0, dtype=torch.float64).pin_memory()
+    h_X = torch.empty((n, m0), dtype=torch.complex128).pin_memory()
+    h_Xh = torch.empty((n, m0), dtype=torch.complex128).pin_memory()
+    h2d = rp.numel() * 4 + ci.numel() * 4 + va.numel() * 8 + 2 * Y0.numel() * 16
+    d2h = 0
+    times, found = [], 0
+    reps = max(1, min(args.steps, 3))
+    for k in range(reps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d_rp, d_ci, d_va = rp.to(dev, non_blocking=True), ci.to(dev, non_blocking=True), va.to(dev, non_blocking=True)
+        dY0, dYh0 = Y0.to(dev, non_blocking=True), Yh0.to(dev, non_blocking=True)
+        ctx = F.FeastNH((d_rp, d_ci, d_va, F.R64, n, A.nnz), None, wk.contour, m0, device=dev, precision=prec)
+        out = ctx.solve(dY0, dYh0)
+        mm = out["m"]
+        h_lam[:mm].copy_(out["lam"], non_blocking=True)
+        h_res[:mm].copy_(out["res"], non_blocking=True)
+        h_X[:, :mm].copy_(out["X"], non_blocking=True)
+        h_Xh[:, :mm].copy_(out["Xh"], non_blocking=True)
+        torch.cuda.synchronize()
+        ctx.close()
+        t1 = time.perf_counter()
+        if k > 0:  # first repetition is a warm-up
+            times.append(t1 - t0)
+            found += mm
+            d2h = mm * (16 + 8) + 2 * n * mm * 16
+    return {"value": round(found / sum(times), 4), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(1e3 * sum(times) / len(times), 2),
+            "includes": "H2D CSR + start blocks, init (transposed CSR, workspace), solve, D2H results, destroy"}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle leg
+# ----------------------------------------------------------------------------
+def oracle_sample(wk, iterations, sample_nodes=1):
+    """Time the oracle on `sample_nodes` of the ne nodes (SuperLU factorisation,
+    right and left solves with m0 columns) plus one Rayleigh-Ritz step, and
+    extrapolate to a full solve with `iterations` outer iterations:
+        T = ne*t_fact + iterations*(ne*t_solve + t_rr)."""
+    from oracle import feast_nh as OF
+    from oracle.contour import contour_nodes
+    z, w = contour_nodes(wk.contour)
+    t0 = time.perf_counter()
+    solvers = [OF.NodeSolver(wk.A, None, z[j], dense=False) for j in range(sample_nodes)]
+    t1 = time.perf_counter()
+    Q = np.zeros(wk.Y0.shape, np.complex128)
+    Qh = np.zeros(wk.Y0.shape, np.complex128)
+    for j, s in enumerate(solvers):
+        Q += w[j] * s.solve(wk.Y0)
+        Qh += np.conj(w[j]) * s.solve(wk.Yh0, herm=True)
+    t2 = time.perf_counter()
+    OF.rayleigh_ritz(wk.A, None, Q, Qh, z, w)
+    t3 = time.perf_counter()
+    ne = len(z)
+    t_fact = (t1 - t0) / sample_nodes
+    t_solve = (t2 - t1) / sample_nodes
+    T = ne * t_fact + iterations * (ne * t_solve + (t3 - t2))
+    return T, dict(t_fact=t_fact, t_solve=t_solve, t_rr=t3 - t2, sample_s=t3 - t0)
+
+
+def threads_used():
+    try:
+        from threadpoolctl import threadpool_info
+        return max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(wk, iterations):
+    T, d = oracle_sample(wk, iterations)
+    m = wk.exact.size
+    return {"value": round(m / T, 5), "unit": UNIT, "cores": threads_used(), "kind": "oracle",
+            "sample": (f"oracle (scipy SuperLU per node + numpy RR, FP64) on 1 of {wk.contour.ne} nodes and one "
+                       f"Rayleigh-Ritz step of the same workload ({d['sample_s']:.1f} s), extrapolated to "
+                       f"ne={wk.contour.ne} factorisations + {iterations} iterations x (ne solves + RR) = "
+                       f"{T:.1f} s for m={m}"),
+            "per_phase_s": {k: round(v, 3) for k, v in d.items()}}
+
+
+def run_reference(args, rank, world):
+    from paper_1506_04463_gb300 import workloads as wl
+    if rank != 0:
+        return None
+    wk = wl.config2(N=args.N)
+    iters = 2  # outer iterations this workload needs (both forms of the GPU path and the oracle)
+    vals, samples = [], []
+    for k in range(args.warmup + args.steps):
+        T, d = oracle_sample(wk, iters)
+        if k >= args.warmup:
+            vals.append(wk.exact.size / T)
+            samples.append(d["sample_s"])
+    value = statistics.mean(vals)
+    ms = 1e3 * statistics.mean(samples)
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "form": "CPU oracle (plain FP64 algorithm)", "parallelism": "host cores"},
+            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": threads_used(), "kind": "oracle",
+                             "sample": ("each step: SuperLU of 1 of 16 shifted matrices, right+left solves with "
+                                        "64 columns and one Rayleigh-Ritz step; eigenpairs/s extrapolated to a full "
+                                        "solve of 16 factorisations + 2 iterations")},
+            "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    return line
+
+
+def main():
+    args = parse()
+    rank, world, local_rank = rank_info()
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl")
+        line = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            dist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,186 @@
+/*
+ * feast_nh.h - C ABI of the GB300 (sm_103a) non-Hermitian FEAST hot path.
+ *
+ * Method: Kestyn, Polizzi, Tang, "FEAST eigensolver for non-Hermitian
+ * problems".  For a pencil (A, B) and a contour C the library computes the
+ * eigenvalues inside C with B-bi-orthonormal right and left eigenvectors,
+ *     A X = B X Lambda,   A^H X^ = B^H X^ Lambda^*,   X^^H B X = I,
+ * by subspace iteration with the contour-integration filter
+ *     Q  = sum_j w_j   (z_j B - A)^{-1}   B   Y        (eq. qr)
+ *     Q^ = sum_j w_j^* (z_j B - A)^{-H}   B^H Y^       (eq. ql)
+ * followed by the B-bi-orthonormal Rayleigh-Ritz step (Fig. alg:three).
+ *
+ * Conventions shared by every entry point
+ *  - Matrices are CSR, 0-based, int32 row pointers and column indices, held
+ *    in DEVICE memory owned by the caller; they must stay valid and unchanged
+ *    until feast_nh_destroy.  Column indices within a row need not be sorted;
+ *    duplicates are summed.
+ *  - Dense blocks (Y, Y^, Q, Q^, X, X^) are DEVICE arrays of complex double
+ *    (interleaved re, im), ROW-major n x m with leading dimension m: entry
+ *    (i, c) is at index i*m + c, i.e. a C-contiguous torch tensor of shape
+ *    (n, m) and dtype complex128.  The caller owns them.
+ *  - Small outputs `lambda` (complex, 2 doubles per entry) and `res` are
+ *    DEVICE arrays of length m0; counts and the info struct are HOST memory.
+ *  - All work is enqueued on the stream given to feast_nh_init.  feast_nh_filter
+ *    and the block part of feast_nh_rr are asynchronous; feast_nh_rr and
+ *    feast_nh_solve read a few integers back from the device (subspace size,
+ *    counts, convergence flag) once per call / per outer iteration.
+ *  - The library allocates its workspace in feast_nh_init (and, for the
+ *    banded factors, on the first filter) and frees it in feast_nh_destroy.
+ *  - Errors are returned, never raised or aborted; feast_nh_last_error gives
+ *    a message for the last failing call on a context.  On FEAST_NH_ENOCONV
+ *    the outputs hold the best iterate; on EINVAL/ECUDA they are undefined.
+ */
+#ifndef FEAST_NH_H
+#define FEAST_NH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct feast_nh_ctx feast_nh_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  FEAST_NH_OK = 0,
+  FEAST_NH_EINVAL = 1,    /* bad argument (size, pointer, option)            */
+  FEAST_NH_ENOMEM = 2,    /* device allocation failed                        */
+  FEAST_NH_ECUDA = 3,     /* a CUDA call failed                              */
+  FEAST_NH_ENOCONV = 4,   /* outer iteration cap reached: best iterate kept  */
+  FEAST_NH_EINNER = 5,    /* inner solve did not reach its tolerance         */
+  FEAST_NH_ESINGULAR = 6, /* zero pivot (node on an eigenvalue) or B_Q == 0  */
+  FEAST_NH_ETIMEOUT = 7   /* a bounded device wait gave up                   */
+} feast_nh_status;
+
+typedef enum { FEAST_NH_R64 = 0, FEAST_NH_C64 = 1 } feast_nh_dtype;
+
+/* CSR matrix in device memory (Sec. 3: sparse CSR driver). */
+typedef struct {
+  int32_t n;              /* order                                     */
+  int64_t nnz;            /* number of stored entries                  */
+  const int32_t *rowptr;  /* n+1 entries                               */
+  const int32_t *colind;  /* nnz entries                               */
+  const void *val;        /* nnz doubles (R64) or 2*nnz doubles (C64)  */
+  int32_t dtype;          /* feast_nh_dtype                            */
+} feast_nh_csr;
+
+/* Search contour (Sec. 2.1).  kind 0: circle |z - c| = r.  kind 1: ellipse
+ * z = c + e^{i angle}(r cos t + i ratio*r sin t).  kind 2: custom nodes and
+ * weights z[2*ne], w[2*ne] (HOST arrays of interleaved complex doubles).
+ * Kinds 0 and 1 use the trapezoidal rule with ne half-offset nodes
+ * t_j = pi(2j-1)/ne and weights w_j = z'(t_j)/(i ne) (Sec. 2.3). */
+typedef struct {
+  int32_t kind;
+  double c_re, c_im, r, ratio, angle;
+  int32_t ne;
+  const double *z, *w;
+} feast_nh_contour;
+
+enum { FEAST_NH_INNER_BANDED = 0, FEAST_NH_INNER_BICGSTAB = 1 };
+enum { FEAST_NH_PREC_FP64 = 0, FEAST_NH_PREC_FP32_IR = 1 };
+enum { FEAST_NH_PROBLEM_GENERAL = 0, FEAST_NH_PROBLEM_COMPLEX_SYMMETRIC = 1 };
+
+/* Options.  eps, eta, mu: eq. (res), eq. (resize), Sec. 2.7.  inner_tol is
+ * the relative 2-norm residual each shifted solve must reach (iterative
+ * refinement for FP32_IR, Krylov tolerance for BICGSTAB); inner_max caps
+ * the refinement steps / Krylov iterations. */
+typedef struct {
+  double eps;         /* 1e-10  */
+  double eta;         /* 1e-16  */
+  double mu;          /* 0.1    */
+  double inner_tol;   /* 1e-12  */
+  int32_t max_iter;   /* 100    */
+  int32_t inner_max;  /* 12     */
+  int32_t inner_kind; /* FEAST_NH_INNER_BANDED */
+  int32_t precision;  /* FEAST_NH_PREC_FP64    */
+  int32_t problem;    /* FEAST_NH_PROBLEM_GENERAL */
+  int32_t timing;     /* 1: record CUDA events around the banded solve and
+                         multi-shift kernels; totals go to feast_nh_info   */
+} feast_nh_opts;
+
+/* Per-call record (host).  Times are CUDA-event milliseconds on the stream. */
+typedef struct {
+  int32_t iterations;   /* outer iterations done                              */
+  int32_t m_tilde;      /* subspace size after the last resize                */
+  int32_t m_r;          /* Ritz values inside C at the last iteration         */
+  int32_t m_s;          /* of those, flagged spurious                         */
+  int32_t m;            /* converged pairs returned (m_r - m_s)               */
+  int32_t inner_steps;  /* refinement steps / Krylov iterations, last filter  */
+  int32_t converged;    /* 1 if eq. (res) < eps for the m lowest residuals     */
+  int32_t kl, ku;       /* band of (z B - A) found by the banded inner solver */
+  double max_res;       /* largest of the m lowest residuals                  */
+  double inner_res;     /* largest relative inner residual, last filter       */
+  double t_factor_ms, t_filter_ms, t_rr_ms, t_total_ms;
+  /* with opts.timing: summed device time and launch count of the banded
+   * triangular-solve kernel and of the multi-shift residual kernel */
+  double t_solve_kernel_ms, t_resid_kernel_ms;
+  int32_t n_solve_launches, n_resid_launches;
+} feast_nh_info;
+
+/* Fills *o with the defaults listed above. */
+void feast_nh_default_opts(feast_nh_opts *o);
+
+/* Creates a context for the pencil (A, B) on `contour` with subspace size m0
+ * (1 <= m0 <= 128).  B == NULL means B = I.  `stream` is a cudaStream_t (NULL:
+ * the legacy default stream).  Builds the transposed CSR of A and B for the
+ * left (^H) products and the quadrature nodes; allocates all workspace.
+ * Cite: Fig. alg:three inputs; Sec. 2.1 contour options. */
+feast_nh_status feast_nh_init(feast_nh_ctx **ctx, const feast_nh_csr *A, const feast_nh_csr *B,
+                              const feast_nh_contour *contour, int32_t m0,
+                              const feast_nh_opts *opts, void *stream);
+
+/* Contour integration, step 1 of Fig. alg:three (eq. qr, eq. ql): from the
+ * n x m blocks Y, Yh computes Q and Qh (m <= m0).  Yh/Qh may be NULL for the
+ * complex-symmetric problem, where Qh = conj(Q) (Sec. 2.4).  Factorises the
+ * shifted matrices on first use and keeps the factors (Sec. 4.1 option). */
+feast_nh_status feast_nh_filter(feast_nh_ctx *ctx, const void *Y, const void *Yh, void *Q, void *Qh,
+                                int32_t m);
+
+/* Steps 2-4 of Fig. alg:three on n x m blocks Q, Qh: B_Q, spurious test
+ * against the previous call's Ritz values, eigendecomposition of B_Q,
+ * resize (eq. resize), B-bi-orthonormal U, Uh (eq. uu), reduced problem,
+ * Ritz values `lambda` (device, m complex) and Ritz vectors Y, Yh (n x m_new,
+ * row-major, leading dimension m_new).  Writes the new size to *m_new and,
+ * if info != NULL, m_r/m_s/max_res of the convergence test (step 5). */
+feast_nh_status feast_nh_rr(feast_nh_ctx *ctx, const void *Q, const void *Qh, int32_t m, double *lambda,
+                            void *Y, void *Yh, int32_t *m_new, feast_nh_info *info);
+
+/* The whole method (Fig. alg:three steps 0-5) from start blocks Y0, Yh0
+ * (n x m0; Yh0 ignored for the complex-symmetric problem).  On return the
+ * first *m_found columns of X, Xh (n x m0, leading dimension m0), entries of
+ * lambda (m0 complex) and res (m0 doubles, eq. res) are the converged
+ * eigenpairs inside C, normalised with ||x_i||_2 = 1 (largest entry real
+ * positive) and x^_i^H B x_i = 1.  Returns FEAST_NH_ENOCONV after
+ * opts.max_iter outer iterations. */
+feast_nh_status feast_nh_solve(feast_nh_ctx *ctx, const void *Y0, const void *Yh0, double *lambda,
+                               void *X, void *Xh, double *res, int32_t *m_found, feast_nh_info *info);
+
+/* Number of CUDA kernels this library has launched in this process. */
+uint64_t feast_nh_kernel_launches(void);
+
+/* Frees everything the context owns (not the caller's CSR arrays). */
+void feast_nh_destroy(feast_nh_ctx *ctx);
+
+/* Static description of a status code. */
+const char *feast_nh_strerror(feast_nh_status s);
+
+/* Message of the last failing call on ctx ("" if none). */
+const char *feast_nh_last_error(const feast_nh_ctx *ctx);
+
+/* Quadrature nodes and weights of a contour (host, 2*ne doubles each),
+ * exactly those the filter uses (Sec. 2.3 trapezoidal rule). */
+feast_nh_status feast_nh_nodes(const feast_nh_contour *contour, double *z, double *w);
+
+/* Multi-shift sparse product used as the inner residual, exposed for
+ * measurement: for every node j and column c,
+ *   R_j = B Y - (z_j B - A) X_j       and  Q = sum_j w_j X_j  (if Q != NULL)
+ * with X (ne blocks of n x m, node-major, device complex double), Y (n x m),
+ * R (ne blocks, device complex double).  One pass over A and B. */
+feast_nh_status feast_nh_multishift_residual(feast_nh_ctx *ctx, const void *X, const void *BY, void *R,
+                                             void *Q, int32_t m);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEAST_NH_H */

@@ -1,0 +1,748 @@
+// Banded LU of the shifted matrices (z_j B - A), one per quadrature node, and
+// the triangular solves with it.  This is the direct inner solver of the
+// contour integration (Fig. alg:three step 1; Sec. 3: the banded driver of the
+// paper uses a banded direct solver).  The same factors serve the right solve
+// (eq. qr) and the conjugate-transpose left solve (eq. ql), as Sec. 2.4
+// describes for solvers with a "transpose conjugate solve" feature.
+//
+// No pivoting: for the problems this path targets (real A similar to a
+// symmetric matrix through a diagonal scaling, complex z_j off the real axis)
+// every pivot satisfies |Im pivot| >= |Im z_j| > 0.  A zero pivot is reported.
+//
+// Storage (per node, row-major band): row r, offset t in [0, W), W = kl+ku+1,
+// holds entry (r, r-kl+t); after factorisation t < kl holds L (unit lower) and
+// t >= kl holds U.
+#include <type_traits>
+#include "kernels.h"
+
+// ---------------------------------------------------------------------------
+// band extent and build
+// ---------------------------------------------------------------------------
+__global__ void k_band_extent(CsrView A, int *out) {
+  int kl = 0, ku = 0, bad = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) {
+    for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; ++k) {
+      int c = A.colind[k];
+      if (c < 0 || c >= A.n) { bad = 1; continue; }
+      int d = c - i;
+      if (d < 0) kl = max(kl, -d); else ku = max(ku, d);
+    }
+  }
+  for (int o = 16; o; o >>= 1) {
+    kl = max(kl, __shfl_xor_sync(0xffffffffu, kl, o));
+    ku = max(ku, __shfl_xor_sync(0xffffffffu, ku, o));
+    bad = max(bad, __shfl_xor_sync(0xffffffffu, bad, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(out, kl);
+    atomicMax(out + 1, ku);
+    atomicMax(out + 2, bad);
+  }
+}
+
+void launch_band_extent(const CsrView &A, const CsrView *B, int *d_out, cudaStream_t s) {
+  cudaMemsetAsync(d_out, 0, 3 * sizeof(int), s);
+  int grid = min(1024, ceil_div(A.n, 256));
+  k_band_extent<<<grid, 256, 0, s>>>(A, d_out);
+  note_launch();
+  if (B) {
+    k_band_extent<<<grid, 256, 0, s>>>(*B, d_out);
+    note_launch();
+  }
+}
+
+template <typename T>
+__global__ void k_band_build(CsrView A, CsrView B, int hasB, int kl, int ku, int ne, const cxd *z,
+                             cx<T> *band) {
+  const int n = A.n, W = kl + ku + 1;
+  const size_t ns = (size_t)n * W;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int j = 0; j < ne; ++j) {
+      cx<T> *row = band + j * ns + (size_t)i * W;
+      const cxd zj = z[j];
+      for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; ++k) {
+        int t = A.colind[k] - i + kl;
+        cxd v = csr_val(A, k);
+        row[t] = row[t] - ccast<T>(v);
+      }
+      if (hasB) {
+        for (int64_t k = B.rowptr[i]; k < B.rowptr[i + 1]; ++k) {
+          int t = B.colind[k] - i + kl;
+          row[t] = row[t] + ccast<T>(zj * csr_val(B, k));
+        }
+      } else {
+        row[kl] = row[kl] + ccast<T>(zj);
+      }
+    }
+  }
+}
+
+template <typename T>
+void launch_band_build(const CsrView &A, const CsrView *B, int kl, int ku, int ne, const cxd *d_z, cx<T> *band,
+                       cudaStream_t s) {
+  size_t bytes = (size_t)ne * A.n * (kl + ku + 1) * sizeof(cx<T>);
+  cudaMemsetAsync(band, 0, bytes, s);
+  CsrView Bv = B ? *B : A;
+  k_band_build<T><<<min(4096, ceil_div(A.n, 128)), 128, 0, s>>>(A, Bv, B != nullptr, kl, ku, ne, d_z, band);
+  note_launch();
+}
+template void launch_band_build<double>(const CsrView &, const CsrView *, int, int, int, const cxd *, cxd *,
+                                        cudaStream_t);
+template void launch_band_build<float>(const CsrView &, const CsrView *, int, int, int, const cxd *, cxf *,
+                                       cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// factorisation: blocked right-looking, panel width NB
+// ---------------------------------------------------------------------------
+template <typename T> struct FactorCfg;
+template <> struct FactorCfg<float> { static constexpr int NB = 32; };
+template <> struct FactorCfg<double> { static constexpr int NB = 16; };
+
+template <typename T>
+static size_t panel_smem(int kl, int ku, int NB) {
+  return ((size_t)(NB + kl) * NB + (size_t)NB * ku) * sizeof(cx<T>);
+}
+
+// Factor columns [k, k+nb) (rows [k, k+nb+kl)) and form U12 = L11^{-1} A12
+// (rows [k, k+nb), columns [k+nb, k+nb+ku)).  One CTA per node.
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) k_band_panel(int n, int kl, int ku, int k, cx<T> *band, size_t ns,
+                                                    int *err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T> *P = reinterpret_cast<cx<T> *>(smem_raw);  // (NB+kl) x NB
+  cx<T> *U = P + (size_t)(NB + kl) * NB;             // NB x ku
+  const int W = kl + ku + 1;
+  cx<T> *Bd = band + (size_t)blockIdx.x * ns;
+  const int nb = min(NB, n - k);
+  const int prow = min(n - k, nb + kl);
+  const int ucol = max(0, min(n - k - nb, ku));
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  for (int idx = tid; idx < prow * NB; idx += nt) {
+    int r = idx / NB, c = idx - r * NB;
+    int d = c - r;
+    cx<T> v = mk<T>(0, 0);
+    if (c < nb && d >= -kl && d <= ku) v = Bd[(size_t)(k + r) * W + (d + kl)];
+    P[idx] = v;
+  }
+  for (int idx = tid; idx < nb * ucol; idx += nt) {
+    int r = idx / ucol, c2 = idx - r * ucol;
+    int d = nb + c2 - r;
+    cx<T> v = mk<T>(0, 0);
+    if (d <= ku) v = Bd[(size_t)(k + r) * W + (d + kl)];
+    U[r * ku + c2] = v;
+  }
+  __syncthreads();
+
+  for (int p = 0; p < nb; ++p) {
+    const cx<T> piv = P[p * NB + p];
+    if (piv.re == 0 && piv.im == 0) {
+      if (tid == 0) atomicOr(err, DEVERR_ZERO_PIVOT);
+    }
+    const int iend = min(prow, p + kl + 1);
+    for (int i = p + 1 + tid; i < iend; i += nt) P[i * NB + p] = cdiv(P[i * NB + p], piv);
+    __syncthreads();
+    const int nq = nb - p - 1;
+    if (nq > 0) {
+      const int cnt = (iend - p - 1) * nq;
+      for (int idx = tid; idx < cnt; idx += nt) {
+        int i = p + 1 + idx / nq, q = p + 1 + idx % nq;
+        cfms(P[i * NB + q], P[i * NB + p], P[p * NB + q]);
+      }
+    }
+    __syncthreads();
+  }
+  if (ucol > 0) {
+    for (int p = 0; p < nb - 1; ++p) {
+      const int cnt = (nb - p - 1) * ucol;
+      for (int idx = tid; idx < cnt; idx += nt) {
+        int i = p + 1 + idx / ucol, c2 = idx % ucol;
+        cfms(U[i * ku + c2], P[i * NB + p], U[p * ku + c2]);
+      }
+      __syncthreads();
+    }
+  }
+  for (int idx = tid; idx < prow * NB; idx += nt) {
+    int r = idx / NB, c = idx - r * NB;
+    int d = c - r;
+    if (c < nb && d >= -kl && d <= ku) Bd[(size_t)(k + r) * W + (d + kl)] = P[idx];
+  }
+  for (int idx = tid; idx < nb * ucol; idx += nt) {
+    int r = idx / ucol, c2 = idx - r * ucol;
+    int d = nb + c2 - r;
+    if (d <= ku) Bd[(size_t)(k + r) * W + (d + kl)] = U[r * ku + c2];
+  }
+}
+
+// Trailing update A22 -= L21 * U12 on rows [k+nb, k+nb+kl) x cols [k+nb, k+nb+ku).
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) k_band_update(int n, int kl, int ku, int k, cx<T> *band, size_t ns) {
+  constexpr int TM = 64, TN = 64;
+  __shared__ cx<T> Ls[TM][NB + 1];
+  __shared__ cx<T> Us[NB][TN];
+  const int W = kl + ku + 1;
+  cx<T> *Bd = band + (size_t)blockIdx.z * ns;
+  const int nb = min(NB, n - k);
+  const int r_beg = k + nb, r_end = min(n, k + nb + kl), c_end = min(n, k + nb + ku);
+  const int r0 = r_beg + blockIdx.y * TM, c0 = r_beg + blockIdx.x * TN;
+  if (r0 >= r_end || c0 >= c_end) return;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < TM * NB; idx += 256) {
+    int rr = idx / NB, p = idx - rr * NB;
+    int r = r0 + rr, col = k + p;
+    cx<T> v = mk<T>(0, 0);
+    if (r < r_end && p < nb && r - col <= kl) v = Bd[(size_t)r * W + (col - r + kl)];
+    Ls[rr][p] = v;
+  }
+  for (int idx = tid; idx < NB * TN; idx += 256) {
+    int p = idx / TN, cc = idx - p * TN;
+    int row = k + p, c = c0 + cc;
+    cx<T> v = mk<T>(0, 0);
+    if (p < nb && c < c_end && c - row <= ku) v = Bd[(size_t)row * W + (c - row + kl)];
+    Us[p][cc] = v;
+  }
+  __syncthreads();
+  const int ty = tid >> 4, tx = tid & 15;
+  cx<T> acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = mk<T>(0, 0);
+  for (int p = 0; p < nb; ++p) {
+    cx<T> a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = Ls[ty + 16 * i][p];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) b[j] = Us[p][tx + 16 * j];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], b[j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int r = r0 + ty + 16 * i;
+    if (r >= r_end) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int c = c0 + tx + 16 * j;
+      if (c >= c_end) continue;
+      cx<T> &e = Bd[(size_t)r * W + (c - r + kl)];
+      e = e - acc[i][j];
+    }
+  }
+}
+
+template <typename T> bool band_fits(int kl, int ku) {
+  constexpr int NB = FactorCfg<T>::NB;
+  return panel_smem<T>(kl, ku, NB) <= 220 * 1024;
+}
+template bool band_fits<float>(int, int);
+template bool band_fits<double>(int, int);
+
+template <typename T>
+cudaError_t band_factor(int n, int kl, int ku, int ne, cx<T> *band, int *d_err, cudaStream_t s) {
+  constexpr int NB = FactorCfg<T>::NB;
+  const size_t ns = (size_t)n * (kl + ku + 1);
+  const size_t smem = panel_smem<T>(kl, ku, NB);
+  cudaError_t e = cudaFuncSetAttribute(k_band_panel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  for (int k = 0; k < n; k += NB) {
+    k_band_panel<T, NB><<<ne, 256, smem, s>>>(n, kl, ku, k, band, ns, d_err);
+    note_launch();
+    const int nb = min(NB, n - k);
+    const int rows = min(n, k + nb + kl) - (k + nb);
+    const int cols = min(n, k + nb + ku) - (k + nb);
+    if (rows > 0 && cols > 0) {
+      dim3 grid(ceil_div(cols, 64), ceil_div(rows, 64), ne);
+      k_band_update<T, NB><<<grid, 256, 0, s>>>(n, kl, ku, k, band, ns);
+      note_launch();
+    }
+  }
+  return cudaGetLastError();
+}
+template cudaError_t band_factor<float>(int, int, int, int, cxf *, int *, cudaStream_t);
+template cudaError_t band_factor<double>(int, int, int, int, cxd *, int *, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// triangular solves, both sides in one launch
+// ---------------------------------------------------------------------------
+// grid (ceil(m/R), ne, nsides).  Side 0 solves (LU) x = b (right, eq. qr),
+// side 1 solves (LU)^H x = b (left, eq. ql).  Each CTA owns R columns of one
+// node and sweeps all rows: forward with the lower factor, backward with the
+// upper one, blocks of NB rows.  Inside a block the update by earlier blocks
+// is a small GEMM against a ring buffer of the last rows in shared memory;
+// the NB x NB triangle is then solved row by row.
+template <typename T> struct SolveCfg;
+template <> struct SolveCfg<float> { static constexpr int NB = 32, R = 16, RPT = 2; };
+template <> struct SolveCfg<double> { static constexpr int NB = 16, R = 16, RPT = 1; };
+
+struct SolveSides {
+  const void *rhs[2];
+  cxd *X[2];
+};
+
+template <typename T>
+__device__ __forceinline__ cx<T> lower_elem(const cx<T> *Bd, int W, int kl, int ku, bool herm, int r, int i) {
+  // strictly lower part of the forward factor: N -> L(r,i); H -> conj(U(i,r))
+  int d = r - i;
+  if (!herm) {
+    if (d > kl) return mk<T>(0, 0);
+    return Bd[(size_t)r * W + (kl - d)];
+  }
+  if (d > ku) return mk<T>(0, 0);
+  return conj(Bd[(size_t)i * W + (kl + d)]);
+}
+template <typename T>
+__device__ __forceinline__ cx<T> upper_elem(const cx<T> *Bd, int W, int kl, int ku, bool herm, int r, int i) {
+  // strictly upper part of the backward factor: N -> U(r,i); H -> conj(L(i,r))
+  int d = i - r;
+  if (!herm) {
+    if (d > ku) return mk<T>(0, 0);
+    return Bd[(size_t)r * W + (kl + d)];
+  }
+  if (d > kl) return mk<T>(0, 0);
+  return conj(Bd[(size_t)i * W + (kl - d)]);
+}
+
+template <typename T, typename Tin, int NB, int R, int RPT>
+__global__ void __launch_bounds__(R *NB / RPT) k_band_solve(int n, int kl, int ku, const cx<T> *band, size_t bns,
+                                                            SolveSides io, size_t rns, int m, size_t xns, int mode,
+                                                            cx<T> *ysc, const int *skip) {
+  if (skip && *skip) return;
+  constexpr int G = NB / RPT;
+  constexpr int NT = R * G;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int W = kl + ku + 1;
+  const int bwmax = max(kl, ku);
+  const int TW = bwmax + NB;
+  const int RB = ceil_div(bwmax + NB, NB) * NB;
+  cx<T> *Ms = reinterpret_cast<cx<T> *>(smem_raw);
+  cx<T> *ring = Ms + (size_t)NB * TW;
+  cx<T> *dg = ring + (size_t)RB * R;
+
+  const int side = blockIdx.z;
+  const bool herm = side == 1;
+  const int node = blockIdx.y;
+  const int c0 = blockIdx.x * R;
+  const cx<T> *Bd = band + (size_t)node * bns;
+  const cx<Tin> *Rh = reinterpret_cast<const cx<Tin> *>(io.rhs[side]) + (size_t)node * rns;
+  cxd *Xn = io.X[side] + (size_t)node * xns;
+  cx<T> *Ys = ysc + (((size_t)side * gridDim.y + node) * gridDim.x + blockIdx.x) * (size_t)n * R;
+  const int tid = threadIdx.x;
+  const int col = tid % R, rg = tid / R;
+  const int c = c0 + col;
+  const bool cok = c < m;
+
+  cx<T> acc[RPT];
+  // ---------------- forward (lower) ----------------
+  {
+    const int bw = herm ? ku : kl;
+    const int TWl = bw + NB;
+    for (int kb = 0; kb < n; kb += NB) {
+      const int nbk = min(NB, n - kb);
+      const int i0 = kb - bw;
+      if (!herm) {
+        for (int idx = tid; idx < NB * TWl; idx += NT) {
+          int rr = idx / TWl, ii = idx - rr * TWl;
+          int r = kb + rr, i = i0 + ii;
+          cx<T> v = mk<T>(0, 0);
+          if (rr < nbk && i >= 0 && i < r) v = lower_elem(Bd, W, kl, ku, false, r, i);
+          Ms[idx] = v;
+        }
+      } else {
+        for (int idx = tid; idx < NB * TWl; idx += NT) {
+          int ii = idx / NB, rr = idx - ii * NB;
+          int r = kb + rr, i = i0 + ii;
+          cx<T> v = mk<T>(0, 0);
+          if (rr < nbk && i >= 0 && i < r) v = lower_elem(Bd, W, kl, ku, true, r, i);
+          Ms[rr * TWl + ii] = v;
+        }
+      }
+      if (tid < nbk) dg[tid] = herm ? conj(Bd[(size_t)(kb + tid) * W + kl]) : mk<T>(1, 0);
+#pragma unroll
+      for (int s = 0; s < RPT; ++s) {
+        int r = kb + rg + G * s;
+        acc[s] = (r < n && cok) ? ccast<T>(Rh[(size_t)r * m + c]) : mk<T>(0, 0);
+      }
+      __syncthreads();
+      const int istart = max(0, i0);
+      int slot = istart % RB;
+      for (int i = istart; i < kb; ++i) {
+        const cx<T> yv = ring[slot * R + col];
+#pragma unroll
+        for (int s = 0; s < RPT; ++s) cfms(acc[s], Ms[(rg + G * s) * TWl + (i - i0)], yv);
+        if (++slot == RB) slot = 0;
+      }
+      for (int p = 0; p < nbk; ++p) {
+        const int rs = (kb + p) % RB;
+#pragma unroll
+        for (int s = 0; s < RPT; ++s) {
+          if (rg + G * s == p) {
+            cx<T> v = herm ? cdiv(acc[s], dg[p]) : acc[s];
+            ring[rs * R + col] = v;
+            Ys[(size_t)(kb + p) * R + col] = v;
+          }
+        }
+        __syncthreads();
+        const cx<T> yv = ring[rs * R + col];
+#pragma unroll
+        for (int s = 0; s < RPT; ++s) {
+          int rr = rg + G * s;
+          if (rr > p && rr < nbk) cfms(acc[s], Ms[rr * TWl + (kb + p - i0)], yv);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // ---------------- backward (upper) ----------------
+  {
+    const int bw = herm ? kl : ku;
+    const int TWu = bw + NB;
+    const int nblk = ceil_div(n, NB);
+    for (int b = nblk - 1; b >= 0; --b) {
+      const int kb = b * NB;
+      const int nbk = min(NB, n - kb);
+      if (!herm) {
+        for (int idx = tid; idx < NB * TWu; idx += NT) {
+          int rr = idx / TWu, ii = idx - rr * TWu;
+          int r = kb + rr, i = kb + ii;
+          cx<T> v = mk<T>(0, 0);
+          if (rr < nbk && i > r && i < n) v = upper_elem(Bd, W, kl, ku, false, r, i);
+          Ms[idx] = v;
+        }
+      } else {
+        for (int idx = tid; idx < NB * TWu; idx += NT) {
+          int ii = idx / NB, rr = idx - ii * NB;
+          int r = kb + rr, i = kb + ii;
+          cx<T> v = mk<T>(0, 0);
+          if (rr < nbk && i > r && i < n) v = upper_elem(Bd, W, kl, ku, true, r, i);
+          Ms[rr * TWu + ii] = v;
+        }
+      }
+      if (tid < nbk) dg[tid] = herm ? mk<T>(1, 0) : Bd[(size_t)(kb + tid) * W + kl];
+#pragma unroll
+      for (int s = 0; s < RPT; ++s) {
+        int r = kb + rg + G * s;
+        acc[s] = (r < n) ? Ys[(size_t)r * R + col] : mk<T>(0, 0);
+      }
+      __syncthreads();
+      const int iend = min(n, kb + nbk + bw);
+      int slot = (kb + nbk) % RB;
+      for (int i = kb + nbk; i < iend; ++i) {
+        const cx<T> xv = ring[slot * R + col];
+#pragma unroll
+        for (int s = 0; s < RPT; ++s) cfms(acc[s], Ms[(rg + G * s) * TWu + (i - kb)], xv);
+        if (++slot == RB) slot = 0;
+      }
+      for (int p = nbk - 1; p >= 0; --p) {
+        const int rs = (kb + p) % RB;
+#pragma unroll
+        for (int s = 0; s < RPT; ++s) {
+          if (rg + G * s == p) {
+            cx<T> v = herm ? acc[s] : cdiv(acc[s], dg[p]);
+            ring[rs * R + col] = v;
+            if (cok) {
+              cxd *xp = Xn + (size_t)(kb + p) * m + c;
+              cxd vd = ccast<double>(v);
+              *xp = mode ? (*xp + vd) : vd;
+            }
+          }
+        }
+        __syncthreads();
+        const cx<T> xv = ring[rs * R + col];
+#pragma unroll
+        for (int s = 0; s < RPT; ++s) {
+          int rr = rg + G * s;
+          if (rr < p) cfms(acc[s], Ms[rr * TWu + p], xv);
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// FP32 variant with the band range of each row block split across the 8 warps
+// of the CTA.  Each lane keeps a 4 x 4 register tile (rows rl+8q, columns
+// cl+4t) so that the inner loop is bound by FMA, not shared-memory, issue;
+// partial sums are reduced through shared memory and the NB x NB triangle is
+// then solved warp-locally (each warp owns 2 of the R = 16 columns; rows are
+// finalised one by one and broadcast with shuffles, no block barrier).
+namespace ks {
+constexpr int NB = 32, R = 16, WARPS = 8, NT = 32 * WARPS;
+constexpr int RED_LD = R + 1;
+__host__ __device__ inline int tw_pad(int bw) { return (bw + NB) | 1; }
+__host__ __device__ inline int ring_rows(int bw) { return ceil_div(bw + NB, NB) * NB; }
+}  // namespace ks
+
+template <typename Tin>
+__global__ void __launch_bounds__(ks::NT) k_band_solve_ks(int n, int kl, int ku, const cxf *band, size_t bns,
+                                                          SolveSides io, size_t rns, int m, size_t xns, int mode,
+                                                          cxf *ysc, const int *skip) {
+  using namespace ks;
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int W = kl + ku + 1;
+  const int bwmax = max(kl, ku);
+  const int TWP = tw_pad(bwmax);
+  const int RB = ring_rows(bwmax);
+  cxf *Ms = reinterpret_cast<cxf *>(smem_raw);       // NB x TWP
+  cxf *ring = Ms + (size_t)NB * TWP;                   // RB x R
+  cxf *red = ring + (size_t)RB * R;                    // WARPS x NB x RED_LD
+  cxf *dinv = red + (size_t)WARPS * NB * RED_LD;       // NB
+
+  const int side = blockIdx.z;
+  const bool herm = side == 1;
+  const int node = blockIdx.y;
+  const int c0 = blockIdx.x * R;
+  const cxf *Bd = band + (size_t)node * bns;
+  const cx<Tin> *Rh = reinterpret_cast<const cx<Tin> *>(io.rhs[side]) + (size_t)node * rns;
+  cxd *Xn = io.X[side] + (size_t)node * xns;
+  cxf *Ys = ysc + (((size_t)side * gridDim.y + node) * gridDim.x + blockIdx.x) * (size_t)n * R;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // GEMM tile of this lane
+  const int rl = lane >> 2, cl = lane & 3;
+  // triangle ownership: column tc, rows tr and tr+16
+  const int tc = 2 * warp + (lane >> 4), tr = lane & 15;
+  const int gc = c0 + tc;
+  const bool cok = gc < m;
+
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool fwd = pass == 0;
+    const int bw = fwd ? (herm ? ku : kl) : (herm ? kl : ku);
+    const int TWl = bw + NB;
+    const int nblk = ceil_div(n, NB);
+    for (int bi = 0; bi < nblk; ++bi) {
+      const int b = fwd ? bi : nblk - 1 - bi;
+      const int kb = b * NB;
+      const int nbk = min(NB, n - kb);
+      // ---- tile of the factor: Ms[rr][ii] ----
+      //  fwd: column i = kb - bw + ii (strictly lower part)
+      //  bwd: column i = kb + ii       (strictly upper part)
+      const int ibase = fwd ? kb - bw : kb;
+      if (!herm) {
+        for (int rr = warp; rr < NB; rr += WARPS) {
+          const int r = kb + rr;
+          for (int ii = lane; ii < TWl; ii += 32) {
+            const int i = ibase + ii;
+            cxf v = mk(0.f, 0.f);
+            if (rr < nbk) {
+              if (fwd) {
+                if (i >= 0 && i < r && r - i <= kl) v = Bd[(size_t)r * W + (i - r + kl)];
+              } else {
+                if (i > r && i < n && i - r <= ku) v = Bd[(size_t)r * W + (i - r + kl)];
+              }
+            }
+            Ms[rr * TWP + ii] = v;
+          }
+        }
+      } else {
+        for (int ii = warp; ii < TWl; ii += WARPS) {
+          const int i = ibase + ii;
+          const int rr = lane;  // NB == 32
+          const int r = kb + rr;
+          cxf v = mk(0.f, 0.f);
+          if (rr < nbk) {
+            if (fwd) {
+              if (i >= 0 && i < r && r - i <= ku) v = conj(Bd[(size_t)i * W + (r - i + kl)]);
+            } else {
+              if (i > r && i < n && i - r <= kl) v = conj(Bd[(size_t)i * W + (r - i + kl)]);
+            }
+          }
+          Ms[rr * TWP + ii] = v;
+        }
+      }
+      if (tid < nbk) {
+        // 1 / diagonal of this sweep's factor
+        cxf d = mk(1.f, 0.f);
+        if (fwd && herm) d = conj(Bd[(size_t)(kb + tid) * W + kl]);
+        if (!fwd && !herm) d = Bd[(size_t)(kb + tid) * W + kl];
+        dinv[tid] = cdiv(mk(1.f, 0.f), d);
+      }
+      // right-hand side of the rows this lane finalises
+      cxf acc2[2];
+#pragma unroll
+      for (int s2 = 0; s2 < 2; ++s2) {
+        const int r = kb + tr + 16 * s2;
+        if (r < n && cok)
+          acc2[s2] = fwd ? ccast<float>(Rh[(size_t)r * m + gc]) : Ys[(size_t)r * R + tc];
+        else
+          acc2[s2] = mk(0.f, 0.f);
+      }
+      __syncthreads();
+      // ---- GEMM over the rows already solved, split over warps ----
+      int hlo, hhi;
+      if (fwd) {
+        hlo = max(0, kb - bw);
+        hhi = kb;
+      } else {
+        hlo = kb + nbk;
+        hhi = min(n, kb + nbk + bw);
+      }
+      const int len = hhi - hlo;
+      const int per = ceil_div(max(len, 0), WARPS);
+      const int wlo = hlo + warp * per, whi = min(hhi, wlo + per);
+      cxf acc[4][4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) acc[q][t] = mk(0.f, 0.f);
+      if (wlo < whi) {
+        int slot = wlo % RB;
+        for (int i = wlo; i < whi; ++i) {
+          cxf mv[4], yv[4];
+          const int col = i - ibase;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) mv[q] = Ms[(rl + 8 * q) * TWP + col];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) yv[t] = ring[slot * R + cl + 4 * t];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) cfma(acc[q][t], mv[q], yv[t]);
+          if (++slot == RB) slot = 0;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) red[(warp * NB + rl + 8 * q) * RED_LD + cl + 4 * t] = acc[q][t];
+      __syncthreads();
+#pragma unroll
+      for (int s2 = 0; s2 < 2; ++s2) {
+        const int rr = tr + 16 * s2;
+        cxf sum = mk(0.f, 0.f);
+#pragma unroll
+        for (int w = 0; w < WARPS; ++w) sum = sum + red[(w * NB + rr) * RED_LD + tc];
+        acc2[s2] = acc2[s2] - sum;
+      }
+      // ---- warp-local triangle ----
+      const unsigned full = 0xffffffffu;
+      if (fwd) {
+        for (int p = 0; p < nbk; ++p) {
+          const int src = (lane & 16) | (p & 15);
+          const int sp = p >> 4;
+          cxf mine = sp ? acc2[1] : acc2[0];
+          cxf x = mine * dinv[p];
+          x.re = __shfl_sync(full, x.re, src);
+          x.im = __shfl_sync(full, x.im, src);
+          if ((lane & 15) == (p & 15)) {
+            if (sp) acc2[1] = x; else acc2[0] = x;
+          }
+#pragma unroll
+          for (int s2 = 0; s2 < 2; ++s2) {
+            const int rr = tr + 16 * s2;
+            if (rr > p) cfms(acc2[s2], Ms[rr * TWP + bw + p], x);
+          }
+        }
+      } else {
+        for (int p = nbk - 1; p >= 0; --p) {
+          const int src = (lane & 16) | (p & 15);
+          const int sp = p >> 4;
+          cxf mine = sp ? acc2[1] : acc2[0];
+          cxf x = mine * dinv[p];
+          x.re = __shfl_sync(full, x.re, src);
+          x.im = __shfl_sync(full, x.im, src);
+          if ((lane & 15) == (p & 15)) {
+            if (sp) acc2[1] = x; else acc2[0] = x;
+          }
+#pragma unroll
+          for (int s2 = 0; s2 < 2; ++s2) {
+            const int rr = tr + 16 * s2;
+            if (rr < p) cfms(acc2[s2], Ms[rr * TWP + p], x);
+          }
+        }
+      }
+      // ---- publish the block's solution ----
+#pragma unroll
+      for (int s2 = 0; s2 < 2; ++s2) {
+        const int rr = tr + 16 * s2;
+        if (rr < nbk) {
+          const int r = kb + rr;
+          ring[(r % RB) * R + tc] = acc2[s2];
+          if (fwd) {
+            Ys[(size_t)r * R + tc] = acc2[s2];
+          } else if (cok) {
+            cxd *xp = Xn + (size_t)r * m + gc;
+            const cxd vd = ccast<double>(acc2[s2]);
+            *xp = mode ? (*xp + vd) : vd;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+static size_t solve_smem_ks(int kl, int ku) {
+  const int bwmax = kl > ku ? kl : ku;
+  return ((size_t)ks::NB * ks::tw_pad(bwmax) + (size_t)ks::ring_rows(bwmax) * ks::R +
+          (size_t)ks::WARPS * ks::NB * ks::RED_LD + ks::NB) * sizeof(cxf);
+}
+
+template <typename T>
+static size_t solve_smem(int kl, int ku) {
+  constexpr int NB = SolveCfg<T>::NB, R = SolveCfg<T>::R;
+  int bwmax = kl > ku ? kl : ku;
+  int TW = bwmax + NB;
+  int RB = ceil_div(bwmax + NB, NB) * NB;
+  return ((size_t)NB * TW + (size_t)RB * R + NB) * sizeof(cx<T>);
+}
+
+// rhs/X pointers for the two sides are packed by the caller through the
+// globals below (set by band_solve_sides).
+template <typename T, typename Tin>
+cudaError_t band_solve_sides(int n, int kl, int ku, int ne, const cx<T> *band, const cx<Tin> *rhsR,
+                             const cx<Tin> *rhsL, size_t rns, int m, cxd *XR, cxd *XL, size_t xns, int mode,
+                             cx<T> *ysc, const int *skip, cudaStream_t s) {
+  SolveSides io;
+  io.rhs[0] = rhsR;
+  io.rhs[1] = rhsL ? rhsL : rhsR;
+  io.X[0] = XR;
+  io.X[1] = XL ? XL : XR;
+  const int nsides = (rhsL && XL) ? 2 : 1;
+  const size_t bns = (size_t)n * (kl + ku + 1);
+  if constexpr (std::is_same<T, float>::value) {
+    const size_t smem = solve_smem_ks(kl, ku);
+    auto kern = k_band_solve_ks<Tin>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(ceil_div(m, ks::R), ne, nsides);
+    kern<<<grid, ks::NT, smem, s>>>(n, kl, ku, band, bns, io, rns, m, xns, mode, ysc, skip);
+    note_launch();
+  } else {
+    constexpr int NB = SolveCfg<T>::NB, R = SolveCfg<T>::R, RPT = SolveCfg<T>::RPT;
+    constexpr int NT = R * NB / RPT;
+    const size_t smem = solve_smem<T>(kl, ku);
+    auto kern = k_band_solve<T, Tin, NB, R, RPT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(ceil_div(m, R), ne, nsides);
+    kern<<<grid, NT, smem, s>>>(n, kl, ku, band, bns, io, rns, m, xns, mode, ysc, skip);
+    note_launch();
+  }
+  return cudaGetLastError();
+}
+template cudaError_t band_solve_sides<float, float>(int, int, int, int, const cxf *, const cxf *, const cxf *,
+                                                    size_t, int, cxd *, cxd *, size_t, int, cxf *, const int *,
+                                                    cudaStream_t);
+template cudaError_t band_solve_sides<float, double>(int, int, int, int, const cxf *, const cxd *, const cxd *,
+                                                     size_t, int, cxd *, cxd *, size_t, int, cxf *, const int *,
+                                                     cudaStream_t);
+template cudaError_t band_solve_sides<double, double>(int, int, int, int, const cxd *, const cxd *, const cxd *,
+                                                      size_t, int, cxd *, cxd *, size_t, int, cxd *, const int *,
+                                                      cudaStream_t);
+
+template <typename T> size_t band_solve_scratch_elems(int n, int m, int ne) {
+  constexpr int R = SolveCfg<T>::R;
+  return (size_t)2 * ne * ceil_div(m, R) * (size_t)n * R;
+}
+template size_t band_solve_scratch_elems<float>(int, int, int);
+template size_t band_solve_scratch_elems<double>(int, int, int);
+
+template <typename T> bool band_solve_fits(int kl, int ku) {
+  if (std::is_same<T, float>::value) return solve_smem_ks(kl, ku) <= 220 * 1024;
+  return solve_smem<T>(kl, ku) <= 220 * 1024;
+}
+template bool band_solve_fits<float>(int, int);
+template bool band_solve_fits<double>(int, int);

@@ -1,0 +1,539 @@
+// Dense kernels of the Rayleigh-Ritz step (Fig. alg:three steps 2-4):
+//  * tall-skinny projections G = X^H Y (B_Q, A_U, B_U) and block updates
+//    Z = X S (U = Q V Gamma^{-1/2}, Y = U W), FP64 complex;
+//  * single-CTA m x m work (m <= 128): eigendecomposition of a general complex
+//    matrix (Householder Hessenberg reduction, single-shift complex QR with
+//    Wilkinson shifts, back-substitution for the eigenvectors), Gauss-Jordan
+//    inverse, small products.
+#include <float.h>
+#include "kernels.h"
+
+// ---------------------------------------------------------------------------
+// G = X^H Y
+// ---------------------------------------------------------------------------
+constexpr int kGT = 64;   // output tile
+constexpr int kGR = 16;   // rows staged per step
+
+__global__ void __launch_bounds__(256) k_gram_partial(const cxd *__restrict__ X, int ldx, int mx,
+                                                      const cxd *__restrict__ Y, int ldy, int my, int n,
+                                                      int rows_per_chunk, cxd *__restrict__ partial) {
+  __shared__ cxd Xs[kGR][kGT];
+  __shared__ cxd Ys[kGR][kGT];
+  const int chunk = blockIdx.x;
+  const int a0 = blockIdx.y * kGT, b0 = blockIdx.z * kGT;
+  const int rbeg = chunk * rows_per_chunk, rend = min(n, rbeg + rows_per_chunk);
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  cxd acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = mk(0.0, 0.0);
+  for (int r0 = rbeg; r0 < rend; r0 += kGR) {
+    for (int idx = tid; idx < kGR * kGT; idx += 256) {
+      int rr = idx / kGT, cc = idx - rr * kGT;
+      int r = r0 + rr;
+      Xs[rr][cc] = (r < rend && a0 + cc < mx) ? X[(size_t)r * ldx + a0 + cc] : mk(0.0, 0.0);
+      Ys[rr][cc] = (r < rend && b0 + cc < my) ? Y[(size_t)r * ldy + b0 + cc] : mk(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < kGR; ++rr) {
+      cxd xa[4], yb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) xa[i] = Xs[rr][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) yb[j] = Ys[rr][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cfma_cj(acc[i][j], xa[i], yb[j]);
+    }
+    __syncthreads();
+  }
+  cxd *P = partial + (size_t)chunk * mx * my;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int a = a0 + ty + 16 * i;
+    if (a >= mx) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int b = b0 + tx + 16 * j;
+      if (b < my) P[(size_t)a * my + b] = acc[i][j];
+    }
+  }
+}
+
+__global__ void k_gram_reduce(const cxd *partial, int nchunks, int count, cxd *G) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
+    cxd s = mk(0.0, 0.0);
+    for (int c = 0; c < nchunks; ++c) s = s + partial[(size_t)c * count + e];
+    G[e] = s;
+  }
+}
+
+int gram_chunks(int n) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int c = 2 * sms;
+  int byrows = ceil_div(n, 64);
+  return c < byrows ? c : (byrows < 1 ? 1 : byrows);
+}
+
+void gram(const cxd *X, int ldx, int mx, const cxd *Y, int ldy, int my, int n, cxd *G, cxd *partial, int nchunks,
+          cudaStream_t s) {
+  const int rpc = ceil_div(n, nchunks);
+  const int nc = ceil_div(n, rpc);
+  dim3 grid(nc, ceil_div(mx, kGT), ceil_div(my, kGT));
+  k_gram_partial<<<grid, 256, 0, s>>>(X, ldx, mx, Y, ldy, my, n, rpc, partial);
+  note_launch();
+  k_gram_reduce<<<ceil_div(mx * my, 256), 256, 0, s>>>(partial, nc, mx * my, G);
+  note_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Z = X S  (n x mx times mx x mz)
+// ---------------------------------------------------------------------------
+constexpr int kBT = 64, kBK = 16;
+__global__ void __launch_bounds__(256) k_block_small(const cxd *__restrict__ X, int ldx, int mx,
+                                                     const cxd *__restrict__ S, int lds, int mz, int n,
+                                                     cxd *__restrict__ Z, int ldz) {
+  __shared__ cxd Xs[kBT][kBK + 1];
+  __shared__ cxd Ss[kBK][kBT];
+  const int r0 = blockIdx.x * kBT, b0 = blockIdx.y * kBT;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  cxd acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = mk(0.0, 0.0);
+  for (int a0 = 0; a0 < mx; a0 += kBK) {
+    for (int idx = tid; idx < kBT * kBK; idx += 256) {
+      int rr = idx / kBK, aa = idx - rr * kBK;
+      int r = r0 + rr, a = a0 + aa;
+      Xs[rr][aa] = (r < n && a < mx) ? X[(size_t)r * ldx + a] : mk(0.0, 0.0);
+    }
+    for (int idx = tid; idx < kBK * kBT; idx += 256) {
+      int aa = idx / kBT, bb = idx - aa * kBT;
+      int a = a0 + aa, b = b0 + bb;
+      Ss[aa][bb] = (a < mx && b < mz) ? S[(size_t)a * lds + b] : mk(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int aa = 0; aa < kBK; ++aa) {
+      cxd xr[4], sb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) xr[i] = Xs[ty + 16 * i][aa];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) sb[j] = Ss[aa][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cfma(acc[i][j], xr[i], sb[j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int r = r0 + ty + 16 * i;
+    if (r >= n) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int b = b0 + tx + 16 * j;
+      if (b < mz) Z[(size_t)r * ldz + b] = acc[i][j];
+    }
+  }
+}
+
+void block_times_small(const cxd *X, int ldx, int mx, const cxd *S, int lds, int mz, int n, cxd *Z, int ldz,
+                       cudaStream_t s) {
+  dim3 grid(ceil_div(n, kBT), ceil_div(mz, kBT));
+  k_block_small<<<grid, 256, 0, s>>>(X, ldx, mx, S, lds, mz, n, Z, ldz);
+  note_launch();
+}
+
+// ---------------------------------------------------------------------------
+// column 2-norms (partials), conj copy, broadcast
+// ---------------------------------------------------------------------------
+__global__ void k_colnorm2(const cxd *X, int ld, int m, int n, int rows_per_cta, double *partial) {
+  __shared__ double red[256];
+  const int tid = threadIdx.x;
+  const int lanes = 256 / m;
+  const int c = tid % m, lr = tid / m;
+  double a = 0.0;
+  const int rbeg = blockIdx.x * rows_per_cta, rend = min(n, rbeg + rows_per_cta);
+  if (lr < lanes)
+    for (int i = rbeg + lr; i < rend; i += lanes) a += abs2(X[(size_t)i * ld + c]);
+  red[tid] = a;
+  __syncthreads();
+  if (tid < m) {
+    double s = 0.0;
+    for (int l = 0; l < lanes; ++l) s += red[l * m + tid];
+    partial[(size_t)blockIdx.x * m + tid] = s;
+  }
+}
+int launch_colnorm2(const cxd *X, int ld, int m, int n, double *partial, cudaStream_t s) {
+  int g = min(608, ceil_div(n, 64));
+  int rpc = ceil_div(n, g);
+  g = ceil_div(n, rpc);
+  k_colnorm2<<<g, 256, 0, s>>>(X, ld, m, n, rpc, partial);
+  note_launch();
+  return g;
+}
+
+__global__ void k_copy_conj(const cxd *X, cxd *Y, size_t count) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+    Y[e] = conj(X[e]);
+}
+void launch_copy_conj(const cxd *X, cxd *Y, size_t count, cudaStream_t s) {
+  k_copy_conj<<<grid_for(count), 256, 0, s>>>(X, Y, count);
+  note_launch();
+}
+__global__ void k_broadcast(const cxd *X, cxd *Y, size_t count, int copies) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x) {
+    cxd v = X[e];
+    for (int k = 0; k < copies; ++k) Y[(size_t)k * count + e] = v;
+  }
+}
+void launch_broadcast_block(const cxd *X, cxd *Y, size_t count, int copies, cudaStream_t s) {
+  k_broadcast<<<grid_for(count), 256, 0, s>>>(X, Y, count, copies);
+  note_launch();
+}
+
+// ---------------------------------------------------------------------------
+// small products C = op(A) op(B): (m x k) (k x n)
+// ---------------------------------------------------------------------------
+__global__ void k_small_mm(const cxd *A, int opA, const cxd *B, int opB, cxd *C, int m, int k, int n) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * n; e += gridDim.x * blockDim.x) {
+    int i = e / n, j = e - i * n;
+    cxd s = mk(0.0, 0.0);
+    for (int l = 0; l < k; ++l) {
+      cxd a = opA ? conj(A[(size_t)l * m + i]) : A[(size_t)i * k + l];
+      cxd b = opB ? conj(B[(size_t)j * k + l]) : B[(size_t)l * n + j];
+      cfma(s, a, b);
+    }
+    C[e] = s;
+  }
+}
+void small_mm(const cxd *A, int opA, const cxd *B, int opB, cxd *C, int m, int k, int n, cudaStream_t s) {
+  k_small_mm<<<ceil_div(m * n, 128), 128, 0, s>>>(A, opA, B, opB, C, m, k, n);
+  note_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Gauss-Jordan inverse with partial pivoting (one CTA)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) k_small_inv(const cxd *A, int m, cxd *Ainv, cxd *W, int *err) {
+  __shared__ cxd f[kMaxM0];
+  __shared__ double bv[512];
+  __shared__ int bi[512];
+  __shared__ int piv_s;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < m * m; e += nt) {
+    W[e] = A[e];
+    int i = e / m, j = e - i * m;
+    Ainv[e] = mk(i == j ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  for (int p = 0; p < m; ++p) {
+    double best = -1.0;
+    int bidx = p;
+    for (int i = p + tid; i < m; i += nt) {
+      double v = cabs(W[(size_t)i * m + p]);
+      if (v > best) { best = v; bidx = i; }
+    }
+    bv[tid] = best;
+    bi[tid] = bidx;
+    __syncthreads();
+    for (int o = nt / 2; o; o >>= 1) {
+      if (tid < o) {
+        if (bv[tid + o] > bv[tid] || (bv[tid + o] == bv[tid] && bi[tid + o] < bi[tid])) {
+          bv[tid] = bv[tid + o];
+          bi[tid] = bi[tid + o];
+        }
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      piv_s = bi[0];
+      if (!(bv[0] > 0.0)) atomicOr(err, DEVERR_SINGULAR_SMALL);
+    }
+    __syncthreads();
+    const int pr = piv_s;
+    if (pr != p) {
+      for (int j = tid; j < m; j += nt) {
+        cxd t = W[(size_t)p * m + j];
+        W[(size_t)p * m + j] = W[(size_t)pr * m + j];
+        W[(size_t)pr * m + j] = t;
+        t = Ainv[(size_t)p * m + j];
+        Ainv[(size_t)p * m + j] = Ainv[(size_t)pr * m + j];
+        Ainv[(size_t)pr * m + j] = t;
+      }
+    }
+    __syncthreads();
+    const cxd d = W[(size_t)p * m + p];
+    __syncthreads();
+    for (int j = tid; j < m; j += nt) {
+      W[(size_t)p * m + j] = cdiv(W[(size_t)p * m + j], d);
+      Ainv[(size_t)p * m + j] = cdiv(Ainv[(size_t)p * m + j], d);
+    }
+    for (int i = tid; i < m; i += nt) f[i] = W[(size_t)i * m + p];
+    __syncthreads();
+    for (int e = tid; e < m * m; e += nt) {
+      int i = e / m, j = e - i * m;
+      if (i == p) continue;
+      cfms(W[e], f[i], W[(size_t)p * m + j]);
+      cfms(Ainv[e], f[i], Ainv[(size_t)p * m + j]);
+    }
+    __syncthreads();
+  }
+}
+void small_inv(const cxd *A, int m, cxd *Ainv, cxd *work, int *d_err, cudaStream_t s) {
+  k_small_inv<<<1, 512, 0, s>>>(A, m, Ainv, work, d_err);
+  note_launch();
+}
+
+// ---------------------------------------------------------------------------
+// eigendecomposition of a general complex m x m matrix (one CTA)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double cabs1(cxd a) { return fabs(a.re) + fabs(a.im); }
+
+__device__ void block_reduce_sum2(double &a, double *red) {
+  const int tid = threadIdx.x;
+  red[tid] = a;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o; o >>= 1) {
+    if (tid < o) red[tid] += red[tid + o];
+    __syncthreads();
+  }
+  a = red[0];
+  __syncthreads();
+}
+
+// work layout: H (m*m), Z (m*m), E (m*m)
+__global__ void __launch_bounds__(256) k_small_eig(const cxd *A, int m, cxd *lam, cxd *V, cxd *work, int *err) {
+  __shared__ cxd v[kMaxM0];
+  __shared__ cxd u[kMaxM0];
+  __shared__ double red[256];
+  __shared__ cxd gc[kMaxM0];  // rotation sines
+  __shared__ double gcc[kMaxM0];
+  __shared__ int sh_l, sh_hi, sh_done;
+  __shared__ cxd sh_mu;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  cxd *H = work;
+  cxd *Z = work + (size_t)m * m;
+  cxd *E = work + 2 * (size_t)m * m;
+  for (int e = tid; e < m * m; e += nt) {
+    H[e] = A[e];
+    int i = e / m, j = e - i * m;
+    Z[e] = mk(i == j ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  // ---- Householder reduction to upper Hessenberg form: H = Z^H A Z ----
+  for (int k = 0; k + 2 < m; ++k) {
+    const int L = m - k - 1;
+    double nrm2 = 0.0;
+    for (int i = tid; i < L; i += nt) nrm2 += abs2(H[(size_t)(k + 1 + i) * m + k]);
+    block_reduce_sum2(nrm2, red);
+    const double nrm = sqrt(nrm2);
+    if (nrm == 0.0) continue;
+    const cxd x0 = H[(size_t)(k + 1) * m + k];
+    const double ax0 = cabs(x0);
+    const cxd ph = ax0 > 0 ? mk(x0.re / ax0, x0.im / ax0) : mk(1.0, 0.0);
+    const cxd beta = mk(-ph.re * nrm, -ph.im * nrm);
+    for (int i = tid; i < L; i += nt) v[i] = H[(size_t)(k + 1 + i) * m + k];
+    __syncthreads();
+    if (tid == 0) v[0] = v[0] - beta;
+    __syncthreads();
+    double vn2 = 0.0;
+    for (int i = tid; i < L; i += nt) vn2 += abs2(v[i]);
+    block_reduce_sum2(vn2, red);
+    if (vn2 == 0.0) continue;
+    const double sc = 2.0 / vn2;
+    // left: rows k+1.., columns k..m-1
+    for (int j = k + tid; j < m; j += nt) {
+      cxd w = mk(0.0, 0.0);
+      for (int i = 0; i < L; ++i) cfma_cj(w, v[i], H[(size_t)(k + 1 + i) * m + j]);
+      w = sc * w;
+      for (int i = 0; i < L; ++i) cfms(H[(size_t)(k + 1 + i) * m + j], v[i], w);
+    }
+    __syncthreads();
+    // right: all rows, columns k+1..; and Z
+    for (int r = tid; r < 2 * m; r += nt) {
+      cxd *M = r < m ? H : Z;
+      const int rr = r < m ? r : r - m;
+      cxd s = mk(0.0, 0.0);
+      for (int i = 0; i < L; ++i) cfma(s, M[(size_t)rr * m + k + 1 + i], v[i]);
+      s = sc * s;
+      for (int i = 0; i < L; ++i) {
+        cxd &h = M[(size_t)rr * m + k + 1 + i];
+        // h -= s * conj(v_i)
+        h.re -= s.re * v[i].re + s.im * v[i].im;
+        h.im -= s.im * v[i].re - s.re * v[i].im;
+      }
+    }
+    __syncthreads();
+    for (int i = 1 + tid; i < L; i += nt) H[(size_t)(k + 1 + i) * m + k] = mk(0.0, 0.0);
+    if (tid == 0) H[(size_t)(k + 1) * m + k] = beta;
+    __syncthreads();
+  }
+  // ---- shifted QR iteration to upper triangular (Schur) form ----
+  if (tid == 0) {
+    sh_hi = m - 1;
+    sh_done = 0;
+  }
+  __syncthreads();
+  int its = 0, total = 0;
+  const int maxtotal = 40 * m;
+  while (true) {
+    if (tid == 0) {
+      int hi = sh_hi;
+      int l = hi;
+      while (l > 0) {
+        double s = cabs1(H[(size_t)(l - 1) * m + l - 1]) + cabs1(H[(size_t)l * m + l]);
+        double sub = cabs1(H[(size_t)l * m + l - 1]);
+        if (sub <= DBL_EPSILON * s || sub < 1e-300) break;
+        --l;
+      }
+      if (l > 0) H[(size_t)l * m + l - 1] = mk(0.0, 0.0);
+      sh_l = l;
+      if (l == hi) {
+        sh_hi = hi - 1;
+        its = -1;  // signal deflation
+      } else {
+        ++its;
+        ++total;
+        const cxd a = H[(size_t)(hi - 1) * m + hi - 1], b = H[(size_t)(hi - 1) * m + hi];
+        const cxd c = H[(size_t)hi * m + hi - 1], d = H[(size_t)hi * m + hi];
+        cxd mu;
+        if (its % 11 == 10) {
+          mu = d + mk(0.75 * cabs1(c), 0.0);
+        } else {
+          cxd half = mk(0.5 * (a.re - d.re), 0.5 * (a.im - d.im));
+          cxd disc = csqrt(half * half + b * c);
+          cxd mid = mk(0.5 * (a.re + d.re), 0.5 * (a.im + d.im));
+          cxd m1 = mid + disc, m2 = mid - disc;
+          mu = abs2(m1 - d) < abs2(m2 - d) ? m1 : m2;
+        }
+        sh_mu = mu;
+        if (total > maxtotal) {
+          atomicOr(err, DEVERR_QR_NOCONV);
+          sh_done = 1;
+        }
+      }
+      if (sh_hi < 1) sh_done = 1;
+    }
+    __syncthreads();
+    if (sh_done) break;
+    const int l = sh_l, hi = sh_hi;
+    if (its < 0) {  // deflated (thread 0 state); resync its
+      its = 0;
+    }
+    if (l >= hi) {
+      __syncthreads();
+      continue;
+    }
+    const cxd mu = sh_mu;
+    for (int i = l + tid; i <= hi; i += nt) H[(size_t)i * m + i] = H[(size_t)i * m + i] - mu;
+    __syncthreads();
+    for (int k = l; k < hi; ++k) {
+      if (tid == 0) {
+        const cxd a = H[(size_t)k * m + k], b = H[(size_t)(k + 1) * m + k];
+        const double aa = cabs(a), bb = cabs(b);
+        const double rho = hypot(aa, bb);
+        double c;
+        cxd s;
+        if (rho == 0.0) {
+          c = 1.0;
+          s = mk(0.0, 0.0);
+        } else if (aa == 0.0) {
+          c = 0.0;
+          s = mk(b.re / bb, -b.im / bb);
+        } else {
+          c = aa / rho;
+          cxd ph = mk(a.re / aa, a.im / aa);
+          s = (1.0 / rho) * (ph * conj(b));
+        }
+        gcc[k] = c;
+        gc[k] = s;
+      }
+      __syncthreads();
+      const double c = gcc[k];
+      const cxd s = gc[k];
+      for (int j = k + tid; j < m; j += nt) {
+        const cxd h1 = H[(size_t)k * m + j], h2 = H[(size_t)(k + 1) * m + j];
+        H[(size_t)k * m + j] = c * h1 + s * h2;
+        H[(size_t)(k + 1) * m + j] = c * h2 - conj(s) * h1;
+      }
+      __syncthreads();
+    }
+    for (int k = l; k < hi; ++k) {
+      const double c = gcc[k];
+      const cxd s = gc[k];
+      const int rmax = min(k + 2, hi);
+      for (int r = tid; r < m + rmax + 1; r += nt) {
+        cxd *M;
+        int rr;
+        if (r <= rmax) {
+          M = H;
+          rr = r;
+        } else {
+          M = Z;
+          rr = r - rmax - 1;
+        }
+        const cxd h1 = M[(size_t)rr * m + k], h2 = M[(size_t)rr * m + k + 1];
+        M[(size_t)rr * m + k] = c * h1 + conj(s) * h2;
+        M[(size_t)rr * m + k + 1] = c * h2 - s * h1;
+      }
+      __syncthreads();
+    }
+    for (int i = l + tid; i <= hi; i += nt) H[(size_t)i * m + i] = H[(size_t)i * m + i] + mu;
+    __syncthreads();
+  }
+  // ---- eigenvectors of the triangular T = H, then V = Z E ----
+  double tnorm = 0.0;
+  for (int e = tid; e < m * m; e += nt) {
+    int i = e / m, j = e - i * m;
+    if (j >= i) tnorm = fmax(tnorm, cabs1(H[e]));
+  }
+  red[tid] = tnorm;
+  __syncthreads();
+  for (int o = nt / 2; o; o >>= 1) {
+    if (tid < o) red[tid] = fmax(red[tid], red[tid + o]);
+    __syncthreads();
+  }
+  const double small = fmax(red[0], 1e-300) * DBL_EPSILON;
+  __syncthreads();
+  for (int k = tid; k < m; k += nt) {
+    const cxd tk = H[(size_t)k * m + k];
+    for (int j = k + 1; j < m; ++j) E[(size_t)j * m + k] = mk(0.0, 0.0);
+    E[(size_t)k * m + k] = mk(1.0, 0.0);
+    for (int j = k - 1; j >= 0; --j) {
+      cxd s = mk(0.0, 0.0);
+      for (int l2 = j + 1; l2 <= k; ++l2) cfma(s, H[(size_t)j * m + l2], E[(size_t)l2 * m + k]);
+      cxd d = H[(size_t)j * m + j] - tk;
+      if (cabs1(d) < small) d = mk(small, 0.0);
+      E[(size_t)j * m + k] = -cdiv(s, d);
+    }
+    lam[k] = tk;
+  }
+  __syncthreads();
+  for (int e = tid; e < m * m; e += nt) {
+    int i = e / m, k = e - i * m;
+    cxd s = mk(0.0, 0.0);
+    for (int l2 = 0; l2 <= k; ++l2) cfma(s, Z[(size_t)i * m + l2], E[(size_t)l2 * m + k]);
+    V[e] = s;
+  }
+  __syncthreads();
+  for (int k = tid; k < m; k += nt) {
+    double s = 0.0;
+    for (int i = 0; i < m; ++i) s += abs2(V[(size_t)i * m + k]);
+    s = s > 0 ? 1.0 / sqrt(s) : 1.0;
+    for (int i = 0; i < m; ++i) V[(size_t)i * m + k] = s * V[(size_t)i * m + k];
+  }
+}
+
+void small_eig(const cxd *A, int m, cxd *lam, cxd *V, cxd *work, int *d_err, cudaStream_t s) {
+  k_small_eig<<<1, 256, 0, s>>>(A, m, lam, V, work, d_err);
+  note_launch();
+}

@@ -1,0 +1,72 @@
+// Internal launchers shared between the translation units of the library.
+#pragma once
+#include "common.cuh"
+
+// ---------------- band.cu : banded LU of (z_j B - A) -----------------------
+// Row-major band storage: node j, row r, offset t in [0, W), W = kl+ku+1,
+// holds entry (r, r - kl + t) of the matrix / of its L (t < kl) and U (t >= kl)
+// factors.
+void launch_band_extent(const CsrView &A, const CsrView *B, int *d_out, cudaStream_t s);
+template <typename T>
+void launch_band_build(const CsrView &A, const CsrView *B, int kl, int ku, int ne, const cxd *d_z,
+                       cx<T> *band, cudaStream_t s);
+template <typename T>
+cudaError_t band_factor(int n, int kl, int ku, int ne, cx<T> *band, int *d_err, cudaStream_t s);
+// Solve with the factors of every node at once, right side (LU) x = b and,
+// if rhsL/XL are given, left side (LU)^H x = b in the same launch.  rhs:
+// node-major blocks (or one shared block when rns == 0) of n x m with row
+// stride m, element type Tin.  X (double complex, node stride xns) gets the
+// solution (mode 0) or has it added (mode 1).  Skipped when *skip != 0.
+template <typename T, typename Tin>
+cudaError_t band_solve_sides(int n, int kl, int ku, int ne, const cx<T> *band, const cx<Tin> *rhsR,
+                             const cx<Tin> *rhsL, size_t rns, int m, cxd *XR, cxd *XL, size_t xns, int mode,
+                             cx<T> *ysc, const int *skip, cudaStream_t s);
+template <typename T> size_t band_solve_scratch_elems(int n, int m, int ne);
+template <typename T> bool band_fits(int kl, int ku);
+template <typename T> bool band_solve_fits(int kl, int ku);
+
+// ---------------- spmm.cu : sparse products --------------------------------
+// R_j = BY - (z_j B - A) X_j for all nodes j (node-major X, R), optional
+// Q = sum_j w_j X_j, per-CTA partial sums of |R_j,c|^2 into partial
+// [gridDim][ne*m].  Returns the grid size used (for the reduction).
+template <typename Tout>
+int launch_multishift_residual(const CsrView &A, const CsrView *B, int ne, const cxd *d_z, const cxd *d_w,
+                               const cxd *X, const cxd *BY, cx<Tout> *R, cxd *Q, double *partial, int m,
+                               const int *d_skip, cudaStream_t s);
+// Reduce the partial sums into relative residuals ||R_jc|| / ||BY_c|| and set
+// *d_done = 1 when all are <= tol.  bynorm2[c] = ||BY_c||^2.  nsides blocks of
+// partials (each nparts x ne*m) and of bynorm2 (each m) are checked together.
+void launch_residual_check(const double *partial, int nparts, int ne, int m, const double *bynorm2, int nsides,
+                           double tol, double *d_maxrel, int *d_done, cudaStream_t s);
+// Out = M1 X - shift_c (M2 X)  (M2 == NULL: identity), row-major n x m blocks.
+// If p1/p2 != NULL, per-CTA partial column 1-norms of Out and of (M2 X).
+int launch_spmm(const CsrView &M1, const CsrView *M2, const cxd *shift, const cxd *X, cxd *Out, int m,
+                double *p1, double *p2, cudaStream_t s);
+// Largest grid the sparse kernels use (8 CTAs per SM).
+int spmm_max_grid();
+// Column reductions of partial arrays [nparts][m] -> out[m] (fixed order).
+void launch_reduce_parts(const double *parts, int nparts, int m, double *out, cudaStream_t s);
+// Transposed CSR (deterministic: entries of each row ordered by column).
+cudaError_t csr_transpose(const CsrView &A, int32_t *rowptr_t, int32_t *colind_t, double *val_t,
+                          int32_t *work, cudaStream_t s);
+
+// ---------------- dense.cu : tall-skinny and small dense kernels -----------
+// G = X^H Y (mx x my), X: n x mx (ld ldx), Y: n x my (ld ldy); partial buffer
+// of size nchunks*mx*my complex.
+void gram(const cxd *X, int ldx, int mx, const cxd *Y, int ldy, int my, int n, cxd *G, cxd *partial,
+          int nchunks, cudaStream_t s);
+int gram_chunks(int n);
+// Z (n x mz, ld ldz) = X (n x mx, ld ldx) * S (mx x mz, row-major, ld lds)
+void block_times_small(const cxd *X, int ldx, int mx, const cxd *S, int lds, int mz, int n, cxd *Z, int ldz,
+                       cudaStream_t s);
+// Column 2-norms^2 partials of a row-major block.
+int launch_colnorm2(const cxd *X, int ld, int m, int n, double *partial, cudaStream_t s);
+void launch_copy_conj(const cxd *X, cxd *Y, size_t count, cudaStream_t s);
+void launch_broadcast_block(const cxd *X, cxd *Y, size_t count, int copies, cudaStream_t s);
+
+// Small single-CTA work on m x m matrices in global memory (row-major).
+void small_eig(const cxd *A, int m, cxd *lam, cxd *V, cxd *work, int *d_err, cudaStream_t s);
+void small_inv(const cxd *A, int m, cxd *Ainv, cxd *work, int *d_err, cudaStream_t s);
+// C = op(A) * op(B), all m x m (or general k), op: 0 none, 1 conj-transpose.
+void small_mm(const cxd *A, int opA, const cxd *B, int opB, cxd *C, int m, int k, int n, cudaStream_t s);
+

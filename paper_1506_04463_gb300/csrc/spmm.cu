@@ -1,0 +1,340 @@
+// Sparse products of the contour filter and of the Rayleigh-Ritz step.
+//
+//  * k_multishift_residual: one pass over A (and B) applies every shift z_j
+//    to every column: R_j = B Y - (z_j B - A) X_j, the residual of the shifted
+//    systems of eq. (qr) for all quadrature nodes at once, and accumulates the
+//    filtered block Q = sum_j w_j X_j (eq. qr) in fixed node order.
+//  * k_spmm: Out = M1 X - s_c M2 X with a per-column shift, used for B Q,
+//    A U, B U and the eigen-residuals of eq. (res).
+//  * csr transpose for the conjugate-transpose products A^H, B^H (eq. ql and
+//    the left residual of eq. res).
+#include "kernels.h"
+
+template <bool CPLX>
+__device__ __forceinline__ void csr_fma(cxd &acc, const CsrView &M, int64_t k, const cxd &x) {
+  if (CPLX) {
+    cxd v = reinterpret_cast<const cxd *>(M.val)[k];
+    if (M.conj_vals) v.im = -v.im;
+    cfma(acc, v, x);
+  } else {
+    const double v = M.val[k];
+    acc.re = fma(v, x.re, acc.re);
+    acc.im = fma(v, x.im, acc.im);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// multi-shift residual + node accumulation
+// ---------------------------------------------------------------------------
+constexpr int kMsThreads = 256;
+constexpr int kMsMaxPairs = 8;  // ne*m <= 2048
+
+template <typename Tout, bool ACPLX, bool BCPLX>
+__global__ void __launch_bounds__(kMsThreads)
+    k_multishift_residual(CsrView A, CsrView B, int hasB, int ne, const cxd *__restrict__ z,
+                          const cxd *__restrict__ w, const cxd *__restrict__ X, size_t xns,
+                          const cxd *__restrict__ BY, cx<Tout> *__restrict__ R, cxd *__restrict__ Q,
+                          double *__restrict__ partial, int m, int rows_per_cta, const int *skip) {
+  if (skip && *skip) return;
+  __shared__ cxd zs[kMaxNe], ws[kMaxNe];
+  const int tid = threadIdx.x;
+  if (tid < ne) {
+    zs[tid] = z[tid];
+    ws[tid] = w[tid];
+  }
+  __syncthreads();
+  const int P = ne * m;
+  const int n = A.n;
+  const int rbeg = blockIdx.x * rows_per_cta;
+  const int rend = min(n, rbeg + rows_per_cta);
+  double nacc[kMsMaxPairs];
+#pragma unroll
+  for (int q = 0; q < kMsMaxPairs; ++q) nacc[q] = 0.0;
+
+  for (int i = rbeg; i < rend; ++i) {
+    const int64_t ka = A.rowptr[i], kae = A.rowptr[i + 1];
+#pragma unroll
+    for (int q = 0; q < kMsMaxPairs; ++q) {
+      const int pair = tid + kMsThreads * q;
+      if (pair < P) {
+        const int j = pair / m, c = pair - j * m;
+        const cxd *Xj = X + (size_t)j * xns;
+        cxd acc = BY ? BY[(size_t)i * m + c] : mk(0.0, 0.0);
+        cxd bx;
+        if (hasB) {
+          bx = mk(0.0, 0.0);
+          for (int64_t k = B.rowptr[i]; k < B.rowptr[i + 1]; ++k)
+            csr_fma<BCPLX>(bx, B, k, Xj[(size_t)B.colind[k] * m + c]);
+        } else {
+          bx = Xj[(size_t)i * m + c];
+        }
+        cfms(acc, zs[j], bx);
+        for (int64_t k = ka; k < kae; ++k) csr_fma<ACPLX>(acc, A, k, Xj[(size_t)A.colind[k] * m + c]);
+        if (R) R[(size_t)j * xns + (size_t)i * m + c] = ccast<Tout>(acc);
+        nacc[q] += abs2(acc);
+      }
+    }
+    if (Q) {
+      for (int c = tid; c < m; c += kMsThreads) {
+        cxd qv = mk(0.0, 0.0);
+        for (int j = 0; j < ne; ++j) cfma(qv, ws[j], X[(size_t)j * xns + (size_t)i * m + c]);
+        Q[(size_t)i * m + c] = qv;
+      }
+    }
+  }
+  if (partial) {
+#pragma unroll
+    for (int q = 0; q < kMsMaxPairs; ++q) {
+      const int pair = tid + kMsThreads * q;
+      if (pair < P) partial[(size_t)blockIdx.x * P + pair] = nacc[q];
+    }
+  }
+}
+
+int spmm_max_grid() {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms * 8;
+}
+
+static int ms_grid(int n) {
+  int g = spmm_max_grid();
+  if (g > n) g = n;
+  return g < 1 ? 1 : g;
+}
+
+template <typename Tout>
+int launch_multishift_residual(const CsrView &A, const CsrView *B, int ne, const cxd *d_z, const cxd *d_w,
+                               const cxd *X, const cxd *BY, cx<Tout> *R, cxd *Q, double *partial, int m,
+                               const int *d_skip, cudaStream_t s) {
+  const int grid = ms_grid(A.n);
+  const int rpc = ceil_div(A.n, grid);
+  const int g = ceil_div(A.n, rpc);
+  const size_t xns = (size_t)A.n * m;
+  CsrView Bv = B ? *B : A;
+  const bool bc = B ? B->cplx : false;
+#define MS_LAUNCH(AC, BC)                                                                                \
+  k_multishift_residual<Tout, AC, BC><<<g, kMsThreads, 0, s>>>(A, Bv, B != nullptr, ne, d_z, d_w, X, xns, \
+                                                               BY, R, Q, partial, m, rpc, d_skip)
+  if (A.cplx) {
+    if (bc) MS_LAUNCH(true, true); else MS_LAUNCH(true, false);
+  } else {
+    if (bc) MS_LAUNCH(false, true); else MS_LAUNCH(false, false);
+  }
+  note_launch();
+#undef MS_LAUNCH
+  return g;
+}
+template int launch_multishift_residual<double>(const CsrView &, const CsrView *, int, const cxd *, const cxd *,
+                                                const cxd *, const cxd *, cxd *, cxd *, double *, int, const int *,
+                                                cudaStream_t);
+template int launch_multishift_residual<float>(const CsrView &, const CsrView *, int, const cxd *, const cxd *,
+                                               const cxd *, const cxd *, cxf *, cxd *, double *, int, const int *,
+                                               cudaStream_t);
+
+__global__ void k_residual_check(const double *partial, int nparts, int P, int m, const double *bynorm2, int nsides,
+                                 double tol, double *maxrel, int *done) {
+  __shared__ double red[256];
+  double mx = 0.0;
+  for (int sp = threadIdx.x; sp < nsides * P; sp += blockDim.x) {
+    const int side = sp / P, pair = sp - side * P;
+    const double *pb = partial + (size_t)side * nparts * P;
+    double s = 0.0;
+    for (int p = 0; p < nparts; ++p) s += pb[(size_t)p * P + pair];
+    const int c = pair % m;
+    const double d = bynorm2[side * m + c];
+    const double rel = d > 0 ? sqrt(s / d) : sqrt(s);
+    mx = fmax(mx, rel);
+    if (!(rel == rel)) mx = INFINITY;
+  }
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *maxrel = red[0];
+    *done = red[0] <= tol ? 1 : 0;
+  }
+}
+
+void launch_residual_check(const double *partial, int nparts, int ne, int m, const double *bynorm2, int nsides,
+                           double tol, double *d_maxrel, int *d_done, cudaStream_t s) {
+  k_residual_check<<<1, 256, 0, s>>>(partial, nparts, ne * m, m, bynorm2, nsides, tol, d_maxrel, d_done);
+  note_launch();
+}
+
+// ---------------------------------------------------------------------------
+// single-shift products with per-column shift and column 1-norms
+// ---------------------------------------------------------------------------
+template <bool C1, bool C2>
+__global__ void __launch_bounds__(256) k_spmm(CsrView M1, CsrView M2, int hasM2, const cxd *__restrict__ shift,
+                                              const cxd *__restrict__ X, cxd *__restrict__ Out, int m,
+                                              int rows_per_cta, double *p1, double *p2) {
+  __shared__ double r1[256], r2[256];
+  const int tid = threadIdx.x;
+  const int lanes = 256 / m;  // m <= 128 -> lanes >= 2
+  const int c = tid % m, lr = tid / m;
+  const bool active = lr < lanes;
+  const int n = M1.n;
+  const int rbeg = blockIdx.x * rows_per_cta, rend = min(n, rbeg + rows_per_cta);
+  double a1 = 0.0, a2 = 0.0;
+  const cxd sh = (shift && active) ? shift[c] : mk(0.0, 0.0);
+  if (active) {
+    for (int i = rbeg + lr; i < rend; i += lanes) {
+      cxd acc = mk(0.0, 0.0);
+      for (int64_t k = M1.rowptr[i]; k < M1.rowptr[i + 1]; ++k)
+        csr_fma<C1>(acc, M1, k, X[(size_t)M1.colind[k] * m + c]);
+      cxd bx;
+      if (hasM2) {
+        bx = mk(0.0, 0.0);
+        for (int64_t k = M2.rowptr[i]; k < M2.rowptr[i + 1]; ++k)
+          csr_fma<C2>(bx, M2, k, X[(size_t)M2.colind[k] * m + c]);
+      } else {
+        bx = X[(size_t)i * m + c];
+      }
+      if (shift) cfms(acc, sh, bx);
+      Out[(size_t)i * m + c] = acc;
+      a1 += cabs(acc);
+      a2 += cabs(bx);
+    }
+  }
+  if (!p1) return;
+  r1[tid] = a1;
+  r2[tid] = a2;
+  __syncthreads();
+  if (tid < m) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int l = 0; l < lanes; ++l) {
+      s1 += r1[l * m + tid];
+      s2 += r2[l * m + tid];
+    }
+    p1[(size_t)blockIdx.x * m + tid] = s1;
+    if (p2) p2[(size_t)blockIdx.x * m + tid] = s2;
+  }
+}
+
+int launch_spmm(const CsrView &M1, const CsrView *M2, const cxd *shift, const cxd *X, cxd *Out, int m, double *p1,
+                double *p2, cudaStream_t s) {
+  const int grid = ms_grid(M1.n);
+  const int rpc = ceil_div(M1.n, grid);
+  const int g = ceil_div(M1.n, rpc);
+  CsrView M2v = M2 ? *M2 : M1;
+  const bool c2 = M2 ? M2->cplx : false;
+#define SP_LAUNCH(A1, A2) k_spmm<A1, A2><<<g, 256, 0, s>>>(M1, M2v, M2 != nullptr, shift, X, Out, m, rpc, p1, p2)
+  if (M1.cplx) {
+    if (c2) SP_LAUNCH(true, true); else SP_LAUNCH(true, false);
+  } else {
+    if (c2) SP_LAUNCH(false, true); else SP_LAUNCH(false, false);
+  }
+  note_launch();
+#undef SP_LAUNCH
+  return g;
+}
+
+__global__ void k_reduce_parts(const double *parts, int nparts, int m, double *out) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int p = 0; p < nparts; ++p) s += parts[(size_t)p * m + c];
+    out[c] = s;
+  }
+}
+void launch_reduce_parts(const double *parts, int nparts, int m, double *out, cudaStream_t s) {
+  k_reduce_parts<<<ceil_div(m, 256), 256, 0, s>>>(parts, nparts, m, out);
+  note_launch();
+}
+
+// ---------------------------------------------------------------------------
+// deterministic CSR transpose
+// ---------------------------------------------------------------------------
+__global__ void k_count_cols(CsrView A, int32_t *cnt) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x)
+    for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; ++k) atomicAdd(&cnt[A.colind[k]], 1);
+}
+// exclusive scan of cnt[0..n) into out[0..n], single CTA
+__global__ void k_scan(const int32_t *cnt, int n, int32_t *out) {
+  __shared__ int32_t part[1024];
+  const int t = threadIdx.x, nt = blockDim.x;
+  const int chunk = ceil_div(n, nt);
+  const int b = t * chunk, e = min(n, b + chunk);
+  int32_t s = 0;
+  for (int i = b; i < e; ++i) s += cnt[i];
+  part[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    int32_t run = 0;
+    for (int i = 0; i < nt; ++i) {
+      int32_t v = part[i];
+      part[i] = run;
+      run += v;
+    }
+    out[n] = run;
+  }
+  __syncthreads();
+  int32_t run = part[t];
+  for (int i = b; i < e; ++i) {
+    out[i] = run;
+    run += cnt[i];
+  }
+}
+__global__ void k_fill_t(CsrView A, const int32_t *rowptr_t, int32_t *cursor, int32_t *colind_t, double *val_t) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x)
+    for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; ++k) {
+      int c = A.colind[k];
+      int pos = rowptr_t[c] + atomicAdd(&cursor[c], 1);
+      colind_t[pos] = i;
+      if (A.cplx) {
+        val_t[2 * (size_t)pos] = A.val[2 * k];
+        val_t[2 * (size_t)pos + 1] = A.val[2 * k + 1];
+      } else {
+        val_t[pos] = A.val[k];
+      }
+    }
+}
+__global__ void k_sort_rows(int n, const int32_t *rowptr, int32_t *colind, double *val, int cplx) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const int b = rowptr[r], e = rowptr[r + 1];
+    for (int i = b + 1; i < e; ++i) {
+      int key = colind[i];
+      double v0 = cplx ? val[2 * (size_t)i] : val[i];
+      double v1 = cplx ? val[2 * (size_t)i + 1] : 0.0;
+      int j = i - 1;
+      while (j >= b && colind[j] > key) {
+        colind[j + 1] = colind[j];
+        if (cplx) {
+          val[2 * (size_t)(j + 1)] = val[2 * (size_t)j];
+          val[2 * (size_t)(j + 1) + 1] = val[2 * (size_t)j + 1];
+        } else {
+          val[j + 1] = val[j];
+        }
+        --j;
+      }
+      colind[j + 1] = key;
+      if (cplx) {
+        val[2 * (size_t)(j + 1)] = v0;
+        val[2 * (size_t)(j + 1) + 1] = v1;
+      } else {
+        val[j + 1] = v0;
+      }
+    }
+  }
+}
+
+cudaError_t csr_transpose(const CsrView &A, int32_t *rowptr_t, int32_t *colind_t, double *val_t, int32_t *work,
+                          cudaStream_t s) {
+  const int n = A.n;
+  const int grid = min(4096, ceil_div(n, 256));
+  cudaMemsetAsync(work, 0, (size_t)n * sizeof(int32_t), s);
+  k_count_cols<<<grid, 256, 0, s>>>(A, work);
+  note_launch();
+  k_scan<<<1, 1024, 0, s>>>(work, n, rowptr_t);
+  note_launch();
+  cudaMemsetAsync(work, 0, (size_t)n * sizeof(int32_t), s);
+  k_fill_t<<<grid, 256, 0, s>>>(A, rowptr_t, work, colind_t, val_t);
+  note_launch();
+  k_sort_rows<<<grid, 256, 0, s>>>(n, rowptr_t, colind_t, val_t, A.cplx);
+  note_launch();
+  return cudaGetLastError();
+}

@@ -1,0 +1,251 @@
+"""Python binding of the C ABI in include/feast_nh.h (argument marshalling only).
+
+Every numerical step runs in libfeast_nh.so.  If the library is missing the
+binding raises; there is no fallback path.  Device memory and streams come
+from PyTorch.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfeast_nh.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EINNER, ESINGULAR, ETIMEOUT = range(8)
+R64, C64 = 0, 1
+INNER_BANDED, INNER_BICGSTAB = 0, 1
+PREC_FP64, PREC_FP32_IR = 0, 1
+PROBLEM_GENERAL, PROBLEM_COMPLEX_SYMMETRIC = 0, 1
+
+
+class Csr(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int64), ("rowptr", C.c_void_p), ("colind", C.c_void_p),
+                ("val", C.c_void_p), ("dtype", C.c_int32)]
+
+
+class ContourS(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("c_re", C.c_double), ("c_im", C.c_double), ("r", C.c_double),
+                ("ratio", C.c_double), ("angle", C.c_double), ("ne", C.c_int32),
+                ("z", C.POINTER(C.c_double)), ("w", C.POINTER(C.c_double))]
+
+
+class Opts(C.Structure):
+    _fields_ = [("eps", C.c_double), ("eta", C.c_double), ("mu", C.c_double), ("inner_tol", C.c_double),
+                ("max_iter", C.c_int32), ("inner_max", C.c_int32), ("inner_kind", C.c_int32),
+                ("precision", C.c_int32), ("problem", C.c_int32), ("timing", C.c_int32)]
+
+
+class Info(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("m_tilde", C.c_int32), ("m_r", C.c_int32), ("m_s", C.c_int32),
+                ("m", C.c_int32), ("inner_steps", C.c_int32), ("converged", C.c_int32), ("kl", C.c_int32),
+                ("ku", C.c_int32), ("max_res", C.c_double), ("inner_res", C.c_double),
+                ("t_factor_ms", C.c_double), ("t_filter_ms", C.c_double), ("t_rr_ms", C.c_double),
+                ("t_total_ms", C.c_double), ("t_solve_kernel_ms", C.c_double), ("t_resid_kernel_ms", C.c_double),
+                ("n_solve_launches", C.c_int32), ("n_resid_launches", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = ["feast_nh_default_opts", "feast_nh_init", "feast_nh_filter", "feast_nh_rr", "feast_nh_solve",
+           "feast_nh_destroy", "feast_nh_strerror", "feast_nh_last_error", "feast_nh_nodes",
+           "feast_nh_multishift_residual", "feast_nh_kernel_launches"]
+
+_lib = None
+
+
+def lib():
+    """Load libfeast_nh.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1506_04463_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, i32 = C.c_void_p, C.c_int32
+    L.feast_nh_default_opts.argtypes = [C.POINTER(Opts)]
+    L.feast_nh_default_opts.restype = None
+    L.feast_nh_init.argtypes = [C.POINTER(vp), C.POINTER(Csr), C.POINTER(Csr), C.POINTER(ContourS), i32,
+                                C.POINTER(Opts), vp]
+    L.feast_nh_filter.argtypes = [vp, vp, vp, vp, vp, i32]
+    L.feast_nh_rr.argtypes = [vp, vp, vp, i32, vp, vp, vp, C.POINTER(i32), C.POINTER(Info)]
+    L.feast_nh_solve.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.POINTER(i32), C.POINTER(Info)]
+    L.feast_nh_destroy.argtypes = [vp]
+    L.feast_nh_destroy.restype = None
+    L.feast_nh_strerror.argtypes = [i32]
+    L.feast_nh_strerror.restype = C.c_char_p
+    L.feast_nh_last_error.argtypes = [vp]
+    L.feast_nh_last_error.restype = C.c_char_p
+    L.feast_nh_nodes.argtypes = [C.POINTER(ContourS), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.feast_nh_multishift_residual.argtypes = [vp, vp, vp, vp, vp, i32]
+    L.feast_nh_kernel_launches.argtypes = []
+    L.feast_nh_kernel_launches.restype = C.c_uint64
+    for f in ("feast_nh_init", "feast_nh_filter", "feast_nh_rr", "feast_nh_solve", "feast_nh_nodes",
+              "feast_nh_multishift_residual"):
+        getattr(L, f).restype = i32
+    _lib = L
+    return L
+
+
+class FeastError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{lib().feast_nh_strerror(status).decode()}: {msg}")
+        self.status = status
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib().feast_nh_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def contour_struct(con) -> tuple[ContourS, list]:
+    """Marshal a workloads.Contour (or any object with the same fields)."""
+    keep = []
+    s = ContourS()
+    s.kind = int(con.kind)
+    s.c_re, s.c_im = float(complex(con.center).real), float(complex(con.center).imag)
+    s.r = float(con.r)
+    s.ratio = float(getattr(con, "ratio", 1.0))
+    s.angle = float(getattr(con, "angle", 0.0))
+    s.ne = int(con.ne if con.kind != 2 else len(con.z))
+    if con.kind == 2:
+        z = np.ascontiguousarray(np.asarray(con.z, np.complex128)).view(np.float64)
+        w = np.ascontiguousarray(np.asarray(con.w, np.complex128)).view(np.float64)
+        keep += [z, w]
+        s.z = z.ctypes.data_as(C.POINTER(C.c_double))
+        s.w = w.ctypes.data_as(C.POINTER(C.c_double))
+    return s, keep
+
+
+def kernel_launches() -> int:
+    """Kernels libfeast_nh.so has launched in this process."""
+    return int(lib().feast_nh_kernel_launches())
+
+
+def nodes(con):
+    """Quadrature nodes/weights exactly as the library computes them."""
+    s, keep = contour_struct(con)
+    z = np.zeros(2 * s.ne)
+    w = np.zeros(2 * s.ne)
+    st = lib().feast_nh_nodes(C.byref(s), z.ctypes.data_as(C.POINTER(C.c_double)),
+                              w.ctypes.data_as(C.POINTER(C.c_double)))
+    if st != OK:
+        raise FeastError(st, "feast_nh_nodes")
+    return z.view(np.complex128), w.view(np.complex128)
+
+
+def csr_to_device(M, device="cuda"):
+    """Upload a scipy CSR matrix as int32 rowptr/colind and float64/complex128 values."""
+    M = M.tocsr()
+    rp = torch.from_numpy(M.indptr.astype(np.int32)).to(device)
+    ci = torch.from_numpy(M.indices.astype(np.int32)).to(device)
+    if np.iscomplexobj(M.data) and np.any(M.data.imag != 0):
+        val = torch.from_numpy(np.ascontiguousarray(M.data.astype(np.complex128))).to(device)
+        dt = C64
+    else:
+        val = torch.from_numpy(np.ascontiguousarray(M.data.real.astype(np.float64))).to(device)
+        dt = R64
+    return (rp, ci, val, dt, M.shape[0], M.nnz)
+
+
+def _csr_struct(t) -> Csr:
+    rp, ci, val, dt, n, nnz = t
+    return Csr(n, nnz, rp.data_ptr(), ci.data_ptr(), val.data_ptr(), dt)
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+class FeastNH:
+    """One context of the C ABI: pencil (A, B), contour, subspace size m0."""
+
+    def __init__(self, A, B, contour, m0, device="cuda", stream=None, **opts):
+        L = lib()
+        self.device = torch.device(device)
+        self.A_dev = A if isinstance(A, tuple) else csr_to_device(A, self.device)
+        self.B_dev = None if B is None else (B if isinstance(B, tuple) else csr_to_device(B, self.device))
+        self.n = self.A_dev[4]
+        self.m0 = int(m0)
+        self.opts = default_opts(**opts)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        cs, self._keep = contour_struct(contour)
+        self.ne = cs.ne
+        a = _csr_struct(self.A_dev)
+        b = _csr_struct(self.B_dev) if self.B_dev is not None else None
+        h = C.c_void_p()
+        st = L.feast_nh_init(C.byref(h), C.byref(a), C.byref(b) if b is not None else None, C.byref(cs),
+                             self.m0, C.byref(self.opts), C.c_void_p(self.stream.cuda_stream))
+        if st != OK:
+            raise FeastError(st, "feast_nh_init (see argument checks)")
+        self.h = h
+
+    def _check(self, st, what):
+        if st not in (OK, ENOCONV):
+            raise FeastError(st, f"{what}: {lib().feast_nh_last_error(self.h).decode()}")
+        return st
+
+    def _blk(self, m):
+        return torch.empty((self.n, m), dtype=torch.complex128, device=self.device)
+
+    def filter(self, Y, Yh=None):
+        m = Y.shape[1]
+        Q, Qh = self._blk(m), self._blk(m)
+        st = lib().feast_nh_filter(self.h, _ptr(Y.contiguous()), _ptr(None if Yh is None else Yh.contiguous()),
+                                   _ptr(Q), _ptr(Qh), m)
+        self._check(st, "feast_nh_filter")
+        return Q, Qh
+
+    def rr(self, Q, Qh):
+        m = Q.shape[1]
+        lam = torch.empty(m, dtype=torch.complex128, device=self.device)
+        Y, Yh = self._blk(m), self._blk(m)
+        mn = C.c_int32()
+        info = Info()
+        st = lib().feast_nh_rr(self.h, _ptr(Q.contiguous()), _ptr(Qh.contiguous()), m, _ptr(lam), _ptr(Y),
+                               _ptr(Yh), C.byref(mn), C.byref(info))
+        self._check(st, "feast_nh_rr")
+        k = mn.value
+        # Y, Yh hold n x k row-major blocks with leading dimension k
+        Yk = Y.view(-1)[: self.n * k].view(self.n, k)
+        Yhk = Yh.view(-1)[: self.n * k].view(self.n, k)
+        return lam[:k], Yk, Yhk, info.as_dict()
+
+    def solve(self, Y0, Yh0=None):
+        lam = torch.zeros(self.m0, dtype=torch.complex128, device=self.device)
+        res = torch.zeros(self.m0, dtype=torch.float64, device=self.device)
+        X, Xh = self._blk(self.m0), self._blk(self.m0)
+        mf = C.c_int32()
+        info = Info()
+        st = lib().feast_nh_solve(self.h, _ptr(Y0.contiguous()), _ptr(None if Yh0 is None else Yh0.contiguous()),
+                                  _ptr(lam), _ptr(X), _ptr(Xh), _ptr(res), C.byref(mf), C.byref(info))
+        self._check(st, "feast_nh_solve")
+        m = mf.value
+        return dict(status=st, lam=lam[:m], X=X[:, :m], Xh=Xh[:, :m], res=res[:m], m=m, info=info.as_dict())
+
+    def multishift_residual(self, X, BY, want_q=True):
+        ne, n, m = X.shape
+        R = torch.empty_like(X)
+        Q = self._blk(m) if want_q else None
+        st = lib().feast_nh_multishift_residual(self.h, _ptr(X.contiguous()), _ptr(BY.contiguous()), _ptr(R),
+                                                _ptr(Q), m)
+        self._check(st, "feast_nh_multishift_residual")
+        return R, Q
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().feast_nh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

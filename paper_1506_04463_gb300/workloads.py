@@ -222,8 +222,9 @@ def banded_random(n: int, kl: int, ku: int, seed: int, complex_: bool = True) ->
 
 def pencil_workload(n: int, seed: int, ne: int = 8, m0: int = 8, complex_: bool = True,
                     with_b: bool = True, n_inside: int = 3) -> Workload:
-    """Tiny dense pencil with a circle around the n_inside eigenvalues nearest
-    the spectrum's centroid; the radius sits halfway to the next eigenvalue.
+    """Tiny dense pencil with a circle around the (at least) n_inside eigenvalues
+    nearest the spectrum's centroid; the radius sits halfway across the first
+    gap of at least 10% that follows them.
     Eigenvalues of the pencil are needed to place the contour (input
     construction only)."""
     import scipy.linalg as sla
@@ -231,7 +232,12 @@ def pencil_workload(n: int, seed: int, ne: int = 8, m0: int = 8, complex_: bool 
     ev = sla.eigvals(A.toarray(), None if B is None else B.toarray())
     c = np.mean(ev)
     d = np.sort(np.abs(ev - c))
-    r = 0.5 * (d[n_inside - 1] + d[n_inside])
+    # the circle passes through a gap of at least 10% of the radius, so that no
+    # eigenvalue (e.g. one of a conjugate pair) lies on or near the contour
+    k = n_inside
+    while k < n - 1 and d[k] - d[k - 1] < 0.1 * d[k]:
+        k += 1
+    r = 0.5 * (d[k - 1] + d[k])
     con = Contour(0, complex(c), float(r), ne=ne)
     return Workload(f"pencil_n{n}_s{seed}", A, B, con, m0,
                     start_block(n, m0, 2 * seed, complex_), start_block(n, m0, 2 * seed + 1, complex_),
