@@ -213,3 +213,16 @@ def feast_nh(A, B, con, m0, Y0, Yh0, eps=1e-10, eta=1e-16, mu=0.1, max_iter=100,
                        converged=conv, history=hist, Y=Y, Yh=Yh, lam_all=lam, res_all=res)
             break
     return out
+
+
+def shifted_residuals(A, B, z, w, X, BY):
+    """Plain definition of the residuals of the shifted systems of eq. (qr):
+    R_j = B Y - (z_j B - A) X_j for every node j, and Q = sum_j w_j X_j.
+    X: (ne, n, m) array; BY: (n, m)."""
+    R = np.empty_like(X)
+    Q = np.zeros(X.shape[1:], np.complex128)
+    for j in range(len(z)):
+        BX = _B(B, X[j])
+        R[j] = BY - (z[j] * BX - A @ X[j])
+        Q += w[j] * X[j]
+    return R, Q
