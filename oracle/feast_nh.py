@@ -17,6 +17,9 @@ Readings where the paper is silent (each listed in the design notes):
   * Ritz vectors are scaled to ||y_i||_2 = 1 with y^_i^H B y_i unchanged;
   * the spurious test compares [B_Q]_ii of this iteration with rho_a^2 of
     the previous Ritz value i; m_s counts flagged values that were inside;
+  * the loop stops when the m = m_r - m_s lowest inside residuals are below
+    eps; it then returns every inside pair with residual below eps (a genuine
+    pair flagged from a not-yet-converged previous iterate is kept);
   * complex symmetric problems use Q^ = conj(Q), V^ = conj(V), W^ = conj(W)
     with v^T v = 1 and w^T B_U w = 1 (Sec. 2.4), so that Y^ = conj(Y).
 """
@@ -203,6 +206,10 @@ def feast_nh(A, B, con, m0, Y0, Yh0, eps=1e-10, eta=1e-16, mu=0.1, max_iter=100,
         conv = m >= 1 and bool(np.all(res[top] < eps))                        # 5.c
         h = dict(it=it, m_tilde=rr["m_tilde"], m_r=m_r, m_s=m_s,
                  max_res=float(np.max(res[top])) if m >= 1 else float("inf"))
+        if conv:
+            # 5.d: every inside pair whose residual is below eps is returned
+            # (spurious values do not converge, Sec. 2.7), at least m of them
+            top = idx[res[idx] < eps]
         if record:
             h.update(gamma=rr["gamma"], rho=rr["rho"], lam=lam, res=res)
         hist.append(h)

@@ -174,6 +174,90 @@ __global__ void __launch_bounds__(256) k_band_panel(int n, int kl, int ku, int k
   }
 }
 
+// Register form of the panel step for bands with NB + kl <= 512: thread i
+// holds row k+i of the panel (columns [k, k+nb)) in registers; the pivot row
+// of each elimination step is published through a double-buffered shared
+// row, so each column costs one barrier.  U12 is formed by k_band_u12.
+template <typename T, int NB>
+__global__ void __launch_bounds__(512) k_band_panel_reg(int n, int kl, int ku, int k, cx<T> *band, size_t ns,
+                                                         int *err) {
+  __shared__ cx<T> prow_s[2][NB];
+  const int W = kl + ku + 1;
+  cx<T> *Bd = band + (size_t)blockIdx.x * ns;
+  const int nb = min(NB, n - k);
+  const int prow = min(n - k, nb + kl);
+  const int i = threadIdx.x;
+  const bool own = i < prow;
+  cx<T> row[NB];
+#pragma unroll
+  for (int q = 0; q < NB; ++q) {
+    const int d = q - i;
+    row[q] = (own && q < nb && d >= -kl && d <= ku) ? Bd[(size_t)(k + i) * W + (d + kl)] : mk<T>(0, 0);
+  }
+  for (int p = 0; p < nb; ++p) {
+    cx<T> *pr = prow_s[p & 1];
+    if (i == p) {
+#pragma unroll
+      for (int q = 0; q < NB; ++q) pr[q] = row[q];
+    }
+    __syncthreads();
+    if (own && i > p && i - p <= kl) {
+      const cx<T> piv = pr[p];
+      if (piv.re == 0 && piv.im == 0) atomicOr(err, DEVERR_ZERO_PIVOT);
+      cx<T> l;
+#pragma unroll
+      for (int q = 0; q < NB; ++q)
+        if (q == p) l = cdiv(row[q], piv);
+#pragma unroll
+      for (int q = 0; q < NB; ++q) {
+        if (q == p) row[q] = l;
+        if (q > p) cfms(row[q], l, pr[q]);
+      }
+    }
+  }
+  if (own) {
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int d = q - i;
+      if (q < nb && d >= -kl && d <= ku) Bd[(size_t)(k + i) * W + (d + kl)] = row[q];
+    }
+  }
+}
+
+// U12 = L11^{-1} A12 for the panel at column k, one column per thread (no
+// barrier): rows [k, k+nb), columns [k+nb, k+nb+ku).  grid (ceil(ku/128), ne).
+template <typename T, int NB>
+__global__ void __launch_bounds__(128) k_band_u12(int n, int kl, int ku, int k, cx<T> *band, size_t ns) {
+  __shared__ cx<T> L11[NB][NB + 1];
+  const int W = kl + ku + 1;
+  cx<T> *Bd = band + (size_t)blockIdx.y * ns;
+  const int nb = min(NB, n - k);
+  const int ucol = max(0, min(n - k - nb, ku));
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, p = e - r * NB;
+    const int d = p - r;
+    L11[r][p] = (r < nb && p < r && -d <= kl) ? Bd[(size_t)(k + r) * W + (d + kl)] : mk<T>(0, 0);
+  }
+  __syncthreads();
+  const int c2 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c2 >= ucol) return;
+  cx<T> col[NB];
+#pragma unroll
+  for (int r = 0; r < NB; ++r) {
+    const int d = nb + c2 - r;
+    col[r] = (r < nb && d <= ku) ? Bd[(size_t)(k + r) * W + (d + kl)] : mk<T>(0, 0);
+  }
+#pragma unroll
+  for (int r = 1; r < NB; ++r)
+#pragma unroll
+    for (int p = 0; p < r; ++p) cfms(col[r], L11[r][p], col[p]);
+#pragma unroll
+  for (int r = 0; r < NB; ++r) {
+    const int d = nb + c2 - r;
+    if (r < nb && d <= ku) Bd[(size_t)(k + r) * W + (d + kl)] = col[r];
+  }
+}
+
 // Trailing update A22 -= L21 * U12 on rows [k+nb, k+nb+kl) x cols [k+nb, k+nb+ku).
 template <typename T, int NB>
 __global__ void __launch_bounds__(256) k_band_update(int n, int kl, int ku, int k, cx<T> *band, size_t ns) {
@@ -245,11 +329,25 @@ cudaError_t band_factor(int n, int kl, int ku, int ne, cx<T> *band, int *d_err, 
   constexpr int NB = FactorCfg<T>::NB;
   const size_t ns = (size_t)n * (kl + ku + 1);
   const size_t smem = panel_smem<T>(kl, ku, NB);
-  cudaError_t e = cudaFuncSetAttribute(k_band_panel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  const bool reg = NB + kl <= 512;
+  const int reg_threads = ceil_div(NB + kl, 32) * 32;
+  if (!reg) {
+    cudaError_t e = cudaFuncSetAttribute(k_band_panel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   for (int k = 0; k < n; k += NB) {
-    k_band_panel<T, NB><<<ne, 256, smem, s>>>(n, kl, ku, k, band, ns, d_err);
-    note_launch();
+    if (reg) {
+      k_band_panel_reg<T, NB><<<ne, reg_threads, 0, s>>>(n, kl, ku, k, band, ns, d_err);
+      note_launch();
+      const int ucol = min(n - k - min(NB, n - k), ku);
+      if (ucol > 0) {
+        k_band_u12<T, NB><<<dim3(ceil_div(ucol, 128), ne), 128, 0, s>>>(n, kl, ku, k, band, ns);
+        note_launch();
+      }
+    } else {
+      k_band_panel<T, NB><<<ne, 256, smem, s>>>(n, kl, ku, k, band, ns, d_err);
+      note_launch();
+    }
     const int nb = min(NB, n - k);
     const int rows = min(n, k + nb + kl) - (k + nb);
     const int cols = min(n, k + nb + ku) - (k + nb);
@@ -462,222 +560,238 @@ __global__ void __launch_bounds__(R *NB / RPT) k_band_solve(int n, int kl, int k
   }
 }
 
-// FP32 variant with the band range of each row block split across the 8 warps
-// of the CTA.  Each lane keeps a 4 x 4 register tile (rows rl+8q, columns
-// cl+4t) so that the inner loop is bound by FMA, not shared-memory, issue;
-// partial sums are reduced through shared memory and the NB x NB triangle is
-// then solved warp-locally (each warp owns 2 of the R = 16 columns; rows are
-// finalised one by one and broadcast with shuffles, no block barrier).
+// FP32 variant.  The band range of each row block is split across the 8 warps
+// of the CTA; each lane keeps a 2 x 4 register tile (rows rl+8q, columns
+// cl+4t).  The factor tile of the next block is fetched with cp.async into a
+// second shared-memory buffer while the current block computes, so the
+// global-memory latency is off the critical path.  Partial sums are reduced
+// through shared memory and the NB x NB triangle is solved warp-locally (each
+// warp owns 2 of the R = 16 columns, one row per lane; rows are finalised in
+// order and broadcast with shuffles).
 namespace ks {
-constexpr int NB = 32, R = 16, WARPS = 8, NT = 32 * WARPS;
+constexpr int NB = 16, R = 16, WARPS = 8, NT = 32 * WARPS;
 constexpr int RED_LD = R + 1;
 __host__ __device__ inline int tw_pad(int bw) { return (bw + NB) | 1; }
 __host__ __device__ inline int ring_rows(int bw) { return ceil_div(bw + NB, NB) * NB; }
 }  // namespace ks
 
-template <typename Tin>
-__global__ void __launch_bounds__(ks::NT) k_band_solve_ks(int n, int kl, int ku, const cxf *band, size_t bns,
-                                                          SolveSides io, size_t rns, int m, size_t xns, int mode,
-                                                          cxf *ysc, const int *skip) {
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int sz = valid ? 8 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Issue the copies of one factor tile (and its diagonal) into shared memory.
+// Step s < nblk: forward block s; s >= nblk: backward block 2*nblk-1-s.
+// N side:  fwd tile (r, i) = L(r, i), i in [kb-kl, r);   diag 1
+//          bwd tile (r, i) = U(r, i), i in (r, r+ku];    diag U(r, r)
+// H side:  fwd tile (r, i) = U(i, r)^*, i in [kb-ku, r); diag U(r, r)^*
+//          bwd tile (r, i) = L(i, r)^*, i in (r, r+kl];  diag 1
+// (conjugation is applied when the tile is read)
+template <bool HERM>
+__device__ __forceinline__ void ks_fetch(const cxf *Bd, int n, int kl, int ku, int W, int nblk, int step, cxf *Mb,
+                                         cxf *db, int TWP) {
   using namespace ks;
-  if (skip && *skip) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const bool fwd = step < nblk;
+  const int b = fwd ? step : 2 * nblk - 1 - step;
+  const int kb = b * NB;
+  const int nbk = min(NB, n - kb);
+  const int bw = fwd ? (HERM ? ku : kl) : (HERM ? kl : ku);
+  const int TWl = bw + NB;
+  const int ibase = fwd ? kb - bw : kb;
+  for (int idx = threadIdx.x; idx < NB * TWl; idx += NT) {
+    int rr, ii;
+    if (!HERM) {
+      rr = idx / TWl;
+      ii = idx - rr * TWl;
+    } else {
+      ii = idx / NB;
+      rr = idx - ii * NB;
+    }
+    const int r = kb + rr, i = ibase + ii;
+    bool ok = rr < nbk && (fwd ? (i >= 0 && i < r && r - i <= bw) : (i > r && i < n && i - r <= bw));
+    const cxf *src = Bd;
+    if (ok) src = HERM ? Bd + (size_t)i * W + (r - i + kl) : Bd + (size_t)r * W + (i - r + kl);
+    cp_async8(Mb + rr * TWP + ii, src, ok);
+  }
+  if (threadIdx.x < NB) {
+    const int rr = threadIdx.x;
+    const bool ok = rr < nbk && (HERM ? fwd : !fwd);
+    cp_async8(db + rr, ok ? Bd + (size_t)(kb + rr) * W + kl : Bd, ok);
+  }
+  cp_async_commit();
+}
+
+template <bool HERM, typename Tin>
+__device__ __forceinline__ void ks_body(int n, int kl, int ku, const cxf *Bd, const cx<Tin> *Rh, cxd *Xn, cxf *Ys,
+                                        int m, int mode, int c0, unsigned char *smem_raw) {
+  using namespace ks;
   const int W = kl + ku + 1;
   const int bwmax = max(kl, ku);
   const int TWP = tw_pad(bwmax);
   const int RB = ring_rows(bwmax);
-  cxf *Ms = reinterpret_cast<cxf *>(smem_raw);       // NB x TWP
-  cxf *ring = Ms + (size_t)NB * TWP;                   // RB x R
+  cxf *Mbuf = reinterpret_cast<cxf *>(smem_raw);      // 2 x NB x TWP
+  cxf *ring = Mbuf + (size_t)2 * NB * TWP;             // RB x R
   cxf *red = ring + (size_t)RB * R;                    // WARPS x NB x RED_LD
-  cxf *dinv = red + (size_t)WARPS * NB * RED_LD;       // NB
-
-  const int side = blockIdx.z;
-  const bool herm = side == 1;
-  const int node = blockIdx.y;
-  const int c0 = blockIdx.x * R;
-  const cxf *Bd = band + (size_t)node * bns;
-  const cx<Tin> *Rh = reinterpret_cast<const cx<Tin> *>(io.rhs[side]) + (size_t)node * rns;
-  cxd *Xn = io.X[side] + (size_t)node * xns;
-  cxf *Ys = ysc + (((size_t)side * gridDim.y + node) * gridDim.x + blockIdx.x) * (size_t)n * R;
+  cxf *dbuf = red + (size_t)WARPS * NB * RED_LD;       // 2 x NB
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // GEMM tile of this lane
   const int rl = lane >> 2, cl = lane & 3;
-  // triangle ownership: column tc, rows tr and tr+16
   const int tc = 2 * warp + (lane >> 4), tr = lane & 15;
   const int gc = c0 + tc;
   const bool cok = gc < m;
+  const int nblk = ceil_div(n, NB);
+  const int nsteps = 2 * nblk;
+  const unsigned full = 0xffffffffu;
 
-  for (int pass = 0; pass < 2; ++pass) {
-    const bool fwd = pass == 0;
-    const int bw = fwd ? (herm ? ku : kl) : (herm ? kl : ku);
-    const int TWl = bw + NB;
-    const int nblk = ceil_div(n, NB);
-    for (int bi = 0; bi < nblk; ++bi) {
-      const int b = fwd ? bi : nblk - 1 - bi;
-      const int kb = b * NB;
-      const int nbk = min(NB, n - kb);
-      // ---- tile of the factor: Ms[rr][ii] ----
-      //  fwd: column i = kb - bw + ii (strictly lower part)
-      //  bwd: column i = kb + ii       (strictly upper part)
-      const int ibase = fwd ? kb - bw : kb;
-      if (!herm) {
-        for (int rr = warp; rr < NB; rr += WARPS) {
-          const int r = kb + rr;
-          for (int ii = lane; ii < TWl; ii += 32) {
-            const int i = ibase + ii;
-            cxf v = mk(0.f, 0.f);
-            if (rr < nbk) {
-              if (fwd) {
-                if (i >= 0 && i < r && r - i <= kl) v = Bd[(size_t)r * W + (i - r + kl)];
-              } else {
-                if (i > r && i < n && i - r <= ku) v = Bd[(size_t)r * W + (i - r + kl)];
-              }
-            }
-            Ms[rr * TWP + ii] = v;
-          }
-        }
-      } else {
-        for (int ii = warp; ii < TWl; ii += WARPS) {
-          const int i = ibase + ii;
-          const int rr = lane;  // NB == 32
-          const int r = kb + rr;
-          cxf v = mk(0.f, 0.f);
-          if (rr < nbk) {
-            if (fwd) {
-              if (i >= 0 && i < r && r - i <= ku) v = conj(Bd[(size_t)i * W + (r - i + kl)]);
-            } else {
-              if (i > r && i < n && i - r <= kl) v = conj(Bd[(size_t)i * W + (r - i + kl)]);
-            }
-          }
-          Ms[rr * TWP + ii] = v;
-        }
-      }
-      if (tid < nbk) {
-        // 1 / diagonal of this sweep's factor
-        cxf d = mk(1.f, 0.f);
-        if (fwd && herm) d = conj(Bd[(size_t)(kb + tid) * W + kl]);
-        if (!fwd && !herm) d = Bd[(size_t)(kb + tid) * W + kl];
-        dinv[tid] = cdiv(mk(1.f, 0.f), d);
-      }
-      // right-hand side of the rows this lane finalises
-      cxf acc2[2];
+  ks_fetch<HERM>(Bd, n, kl, ku, W, nblk, 0, Mbuf, dbuf, TWP);
+  for (int step = 0; step < nsteps; ++step) {
+    const bool fwd = step < nblk;
+    const int b = fwd ? step : 2 * nblk - 1 - step;
+    const int kb = b * NB;
+    const int nbk = min(NB, n - kb);
+    const int bw = fwd ? (HERM ? ku : kl) : (HERM ? kl : ku);
+    const int ibase = fwd ? kb - bw : kb;
+    cxf *Ms = Mbuf + (size_t)(step & 1) * NB * TWP;
+    cxf *dg = dbuf + (step & 1) * NB;
+    // right-hand side of the row this lane finalises
+    cxf acc2 = mk(0.f, 0.f);
+    {
+      const int r = kb + tr;
+      if (r < n && cok) acc2 = fwd ? ccast<float>(Rh[(size_t)r * m + gc]) : Ys[(size_t)r * R + tc];
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (step + 1 < nsteps)
+      ks_fetch<HERM>(Bd, n, kl, ku, W, nblk, step + 1, Mbuf + (size_t)((step + 1) & 1) * NB * TWP,
+                     dbuf + ((step + 1) & 1) * NB, TWP);
+    // ---- GEMM over the rows already solved, split over warps ----
+    int hlo, hhi;
+    if (fwd) {
+      hlo = max(0, kb - bw);
+      hhi = kb;
+    } else {
+      hlo = kb + nbk;
+      hhi = min(n, kb + nbk + bw);
+    }
+    const int len = max(hhi - hlo, 0);
+    const int per = ceil_div(len, WARPS);
+    const int wlo = hlo + warp * per, whi = min(hhi, wlo + per);
+    cxf acc[2][4];
 #pragma unroll
-      for (int s2 = 0; s2 < 2; ++s2) {
-        const int r = kb + tr + 16 * s2;
-        if (r < n && cok)
-          acc2[s2] = fwd ? ccast<float>(Rh[(size_t)r * m + gc]) : Ys[(size_t)r * R + tc];
-        else
-          acc2[s2] = mk(0.f, 0.f);
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) acc[q][t] = mk(0.f, 0.f);
+    if (wlo < whi) {
+      int slot = wlo % RB;
+#pragma unroll 2
+      for (int i = wlo; i < whi; ++i) {
+        cxf mv[2], yv[4];
+        const int col = i - ibase;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          mv[q] = Ms[(rl + 8 * q) * TWP + col];
+          if (HERM) mv[q].im = -mv[q].im;
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) yv[t] = ring[slot * R + cl + 4 * t];
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+          for (int t = 0; t < 4; ++t) cfma(acc[q][t], mv[q], yv[t]);
+        if (++slot == RB) slot = 0;
       }
-      __syncthreads();
-      // ---- GEMM over the rows already solved, split over warps ----
-      int hlo, hhi;
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) red[(warp * NB + rl + 8 * q) * RED_LD + cl + 4 * t] = acc[q][t];
+    __syncthreads();
+    {
+      cxf sum = mk(0.f, 0.f);
+#pragma unroll
+      for (int w = 0; w < WARPS; ++w) sum = sum + red[(w * NB + tr) * RED_LD + tc];
+      acc2 = acc2 - sum;
+    }
+    // ---- warp-local triangle: lane (tc, tr) owns row tr of column tc ----
+    const bool divide = HERM ? fwd : !fwd;
+    if (fwd) {
+      for (int p = 0; p < nbk; ++p) {
+        const int src = (lane & 16) | p;
+        cxf x = acc2;
+        if (divide) {
+          cxf d = dg[p];
+          if (HERM) d.im = -d.im;
+          x = cdiv(x, d);
+        }
+        x.re = __shfl_sync(full, x.re, src);
+        x.im = __shfl_sync(full, x.im, src);
+        if (tr == p) acc2 = x;
+        if (tr > p) {
+          cxf mv = Ms[tr * TWP + bw + p];
+          if (HERM) mv.im = -mv.im;
+          cfms(acc2, mv, x);
+        }
+      }
+    } else {
+      for (int p = nbk - 1; p >= 0; --p) {
+        const int src = (lane & 16) | p;
+        cxf x = acc2;
+        if (divide) {
+          cxf d = dg[p];
+          if (HERM) d.im = -d.im;
+          x = cdiv(x, d);
+        }
+        x.re = __shfl_sync(full, x.re, src);
+        x.im = __shfl_sync(full, x.im, src);
+        if (tr == p) acc2 = x;
+        if (tr < p) {
+          cxf mv = Ms[tr * TWP + p];
+          if (HERM) mv.im = -mv.im;
+          cfms(acc2, mv, x);
+        }
+      }
+    }
+    // ---- publish the block's solution ----
+    if (tr < nbk) {
+      const int r = kb + tr;
+      ring[(r % RB) * R + tc] = acc2;
       if (fwd) {
-        hlo = max(0, kb - bw);
-        hhi = kb;
-      } else {
-        hlo = kb + nbk;
-        hhi = min(n, kb + nbk + bw);
+        Ys[(size_t)r * R + tc] = acc2;
+      } else if (cok) {
+        cxd *xp = Xn + (size_t)r * m + gc;
+        const cxd vd = ccast<double>(acc2);
+        *xp = mode ? (*xp + vd) : vd;
       }
-      const int len = hhi - hlo;
-      const int per = ceil_div(max(len, 0), WARPS);
-      const int wlo = hlo + warp * per, whi = min(hhi, wlo + per);
-      cxf acc[4][4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int t = 0; t < 4; ++t) acc[q][t] = mk(0.f, 0.f);
-      if (wlo < whi) {
-        int slot = wlo % RB;
-        for (int i = wlo; i < whi; ++i) {
-          cxf mv[4], yv[4];
-          const int col = i - ibase;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) mv[q] = Ms[(rl + 8 * q) * TWP + col];
-#pragma unroll
-          for (int t = 0; t < 4; ++t) yv[t] = ring[slot * R + cl + 4 * t];
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int t = 0; t < 4; ++t) cfma(acc[q][t], mv[q], yv[t]);
-          if (++slot == RB) slot = 0;
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int t = 0; t < 4; ++t) red[(warp * NB + rl + 8 * q) * RED_LD + cl + 4 * t] = acc[q][t];
-      __syncthreads();
-#pragma unroll
-      for (int s2 = 0; s2 < 2; ++s2) {
-        const int rr = tr + 16 * s2;
-        cxf sum = mk(0.f, 0.f);
-#pragma unroll
-        for (int w = 0; w < WARPS; ++w) sum = sum + red[(w * NB + rr) * RED_LD + tc];
-        acc2[s2] = acc2[s2] - sum;
-      }
-      // ---- warp-local triangle ----
-      const unsigned full = 0xffffffffu;
-      if (fwd) {
-        for (int p = 0; p < nbk; ++p) {
-          const int src = (lane & 16) | (p & 15);
-          const int sp = p >> 4;
-          cxf mine = sp ? acc2[1] : acc2[0];
-          cxf x = mine * dinv[p];
-          x.re = __shfl_sync(full, x.re, src);
-          x.im = __shfl_sync(full, x.im, src);
-          if ((lane & 15) == (p & 15)) {
-            if (sp) acc2[1] = x; else acc2[0] = x;
-          }
-#pragma unroll
-          for (int s2 = 0; s2 < 2; ++s2) {
-            const int rr = tr + 16 * s2;
-            if (rr > p) cfms(acc2[s2], Ms[rr * TWP + bw + p], x);
-          }
-        }
-      } else {
-        for (int p = nbk - 1; p >= 0; --p) {
-          const int src = (lane & 16) | (p & 15);
-          const int sp = p >> 4;
-          cxf mine = sp ? acc2[1] : acc2[0];
-          cxf x = mine * dinv[p];
-          x.re = __shfl_sync(full, x.re, src);
-          x.im = __shfl_sync(full, x.im, src);
-          if ((lane & 15) == (p & 15)) {
-            if (sp) acc2[1] = x; else acc2[0] = x;
-          }
-#pragma unroll
-          for (int s2 = 0; s2 < 2; ++s2) {
-            const int rr = tr + 16 * s2;
-            if (rr < p) cfms(acc2[s2], Ms[rr * TWP + p], x);
-          }
-        }
-      }
-      // ---- publish the block's solution ----
-#pragma unroll
-      for (int s2 = 0; s2 < 2; ++s2) {
-        const int rr = tr + 16 * s2;
-        if (rr < nbk) {
-          const int r = kb + rr;
-          ring[(r % RB) * R + tc] = acc2[s2];
-          if (fwd) {
-            Ys[(size_t)r * R + tc] = acc2[s2];
-          } else if (cok) {
-            cxd *xp = Xn + (size_t)r * m + gc;
-            const cxd vd = ccast<double>(acc2[s2]);
-            *xp = mode ? (*xp + vd) : vd;
-          }
-        }
-      }
-      __syncthreads();
     }
   }
+  cp_async_wait_all();
+}
+
+template <typename Tin>
+__global__ void __launch_bounds__(ks::NT) k_band_solve_ks(int n, int kl, int ku, const cxf *band, size_t bns,
+                                                          SolveSides io, size_t rns, int m, size_t xns, int mode,
+                                                          cxf *ysc, const int *skip) {
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int side = blockIdx.z;
+  const int node = blockIdx.y;
+  const int c0 = blockIdx.x * ks::R;
+  const cxf *Bd = band + (size_t)node * bns;
+  const cx<Tin> *Rh = reinterpret_cast<const cx<Tin> *>(side ? io.rhs[1] : io.rhs[0]) + (size_t)node * rns;
+  cxd *Xn = (side ? io.X[1] : io.X[0]) + (size_t)node * xns;
+  cxf *Ys = ysc + (((size_t)side * gridDim.y + node) * gridDim.x + blockIdx.x) * (size_t)n * ks::R;
+  if (side)
+    ks_body<true, Tin>(n, kl, ku, Bd, Rh, Xn, Ys, m, mode, c0, smem_raw);
+  else
+    ks_body<false, Tin>(n, kl, ku, Bd, Rh, Xn, Ys, m, mode, c0, smem_raw);
 }
 
 static size_t solve_smem_ks(int kl, int ku) {
   const int bwmax = kl > ku ? kl : ku;
-  return ((size_t)ks::NB * ks::tw_pad(bwmax) + (size_t)ks::ring_rows(bwmax) * ks::R +
-          (size_t)ks::WARPS * ks::NB * ks::RED_LD + ks::NB) * sizeof(cxf);
+  return ((size_t)2 * ks::NB * ks::tw_pad(bwmax) + (size_t)ks::ring_rows(bwmax) * ks::R +
+          (size_t)ks::WARPS * ks::NB * ks::RED_LD + 2 * ks::NB) * sizeof(cxf);
 }
 
 template <typename T>

@@ -191,8 +191,14 @@ __global__ void k_converge(RRParams p, int mt, const cxd *lam, const cxd *rho, c
       mx = fmax(mx, rs[ord[i]]);
       if (!(rs[ord[i]] < p.eps)) conv = false;
     }
+    // 5.d: on convergence every inside pair below eps is returned (at least m)
+    int mout = m > 0 ? m : 0;
+    if (conv) {
+      mout = 0;
+      while (mout < mr && rs[ord[mout]] < p.eps) ++mout;
+    }
     st->m_r = mr;
-    st->m = m > 0 ? m : 0;
+    st->m = mout;
     st->conv = conv ? 1 : 0;
     st->max_res = m >= 1 ? mx : INFINITY;
   }

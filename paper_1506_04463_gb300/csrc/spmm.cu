@@ -133,20 +133,23 @@ template int launch_multishift_residual<float>(const CsrView &, const CsrView *,
                                                const cxd *, const cxd *, cxf *, cxd *, double *, int, const int *,
                                                cudaStream_t);
 
-__global__ void k_residual_check(const double *partial, int nparts, int P, int m, const double *bynorm2, int nsides,
-                                 double tol, double *maxrel, int *done) {
-  __shared__ double red[256];
+// Relative residual of every (side, node, column): ||R||_2 / ||B Y||_2, summed
+// over the per-CTA partials in fixed order; the maximum is folded in with an
+// integer atomicMax on the bits of the (non-negative) double, which is
+// order-independent.
+__global__ void k_residual_rel(const double *partial, int nparts, int P, int m, const double *bynorm2, int nsides,
+                               unsigned long long *maxbits) {
+  __shared__ double red[128];
   double mx = 0.0;
-  for (int sp = threadIdx.x; sp < nsides * P; sp += blockDim.x) {
+  const int sp = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sp < nsides * P) {
     const int side = sp / P, pair = sp - side * P;
     const double *pb = partial + (size_t)side * nparts * P;
     double s = 0.0;
     for (int p = 0; p < nparts; ++p) s += pb[(size_t)p * P + pair];
-    const int c = pair % m;
-    const double d = bynorm2[side * m + c];
+    const double d = bynorm2[side * m + pair % m];
     const double rel = d > 0 ? sqrt(s / d) : sqrt(s);
-    mx = fmax(mx, rel);
-    if (!(rel == rel)) mx = INFINITY;
+    mx = (rel == rel) ? rel : INFINITY;
   }
   red[threadIdx.x] = mx;
   __syncthreads();
@@ -154,15 +157,23 @@ __global__ void k_residual_check(const double *partial, int nparts, int P, int m
     if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    *maxrel = red[0];
-    *done = red[0] <= tol ? 1 : 0;
-  }
+  if (threadIdx.x == 0) atomicMax(maxbits, (unsigned long long)__double_as_longlong(red[0]));
+}
+__global__ void k_residual_done(const unsigned long long *maxbits, double tol, double *maxrel, int *done) {
+  const double v = __longlong_as_double((long long)*maxbits);
+  *maxrel = v;
+  *done = v <= tol ? 1 : 0;
 }
 
 void launch_residual_check(const double *partial, int nparts, int ne, int m, const double *bynorm2, int nsides,
                            double tol, double *d_maxrel, int *d_done, cudaStream_t s) {
-  k_residual_check<<<1, 256, 0, s>>>(partial, nparts, ne * m, m, bynorm2, nsides, tol, d_maxrel, d_done);
+  // d_maxrel doubles as the atomic accumulator (bits of a non-negative double)
+  unsigned long long *bits = reinterpret_cast<unsigned long long *>(d_maxrel);
+  cudaMemsetAsync(bits, 0, sizeof(unsigned long long), s);
+  const int total = nsides * ne * m;
+  k_residual_rel<<<ceil_div(total, 128), 128, 0, s>>>(partial, nparts, ne * m, m, bynorm2, nsides, bits);
+  note_launch();
+  k_residual_done<<<1, 1, 0, s>>>(bits, tol, d_maxrel, d_done);
   note_launch();
 }
 
