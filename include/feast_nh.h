@@ -180,6 +180,34 @@ feast_nh_status feast_nh_nodes(const feast_nh_contour *contour, double *z, doubl
 feast_nh_status feast_nh_multishift_residual(feast_nh_ctx *ctx, const void *X, const void *BY, void *R,
                                              void *Q, int32_t m);
 
+/* The multi-shift residual above for callers that cannot allocate device
+ * memory (an application that owns all device memory through its own pool or
+ * budget, a latency-bound loop that cannot take the synchronisation of
+ * cudaMalloc/cudaFree, an embedding whose memory footprint is fixed at
+ * start-up).  The paper has no counterpart: this is an interface variant.
+ *
+ * Computes, with no context and no allocation, for every node j of `contour`
+ * and column c:  R_j = BY - (z_j B - A) X_j,  Q = sum_j w_j X_j (if Q != NULL)
+ * and relres[j*m + c] = ||R_jc||_2 / ||BY_c||_2.  A, B: device CSR as for
+ * feast_nh_init (B == NULL: identity).  X, R: ne node-major blocks of n x m;
+ * BY, Q: n x m; all row-major complex double in device memory, owned by the
+ * caller; relres: ne*m device doubles.  Enqueued on `stream` (cudaStream_t).
+ *
+ * Scratch: a file-scope device array of 4.6 MiB (quadrature nodes, column
+ * norms, partial sums of at most 256 CTAs) that every GPU loading the library
+ * holds until exit.  Limits: 1 <= m <= 128, 1 <= ne <= 64, ne*m <= 2048;
+ * larger sizes, NULL blocks or bad CSR descriptors return FEAST_NH_EINVAL
+ * before any device work.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current) and caches
+ * it; make that first call before any stream capture.  All calls share the
+ * array: calls that overlap on the GPU (other streams, other threads) race,
+ * so serialise them.  Every scratch entry a call reads is written earlier in
+ * the same call, so nothing carries over between calls. */
+feast_nh_status feast_nh_multishift_residual_noalloc(const feast_nh_csr *A, const feast_nh_csr *B,
+                                                     const feast_nh_contour *contour, const void *X,
+                                                     const void *BY, void *R, void *Q, double *relres,
+                                                     int32_t m, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,6 +33,11 @@ template <typename Tout>
 int launch_multishift_residual(const CsrView &A, const CsrView *B, int ne, const cxd *d_z, const cxd *d_w,
                                const cxd *X, const cxd *BY, cx<Tout> *R, cxd *Q, double *partial, int m,
                                const int *d_skip, cudaStream_t s);
+// As above with at most max_grid CTAs (partial holds max_grid * ne * m doubles).
+template <typename Tout>
+int launch_multishift_residual_capped(const CsrView &A, const CsrView *B, int ne, const cxd *d_z, const cxd *d_w,
+                                      const cxd *X, const cxd *BY, cx<Tout> *R, cxd *Q, double *partial, int m,
+                                      int max_grid, cudaStream_t s);
 // Reduce the partial sums into relative residuals ||R_jc|| / ||BY_c|| and set
 // *d_done = 1 when all are <= tol.  bynorm2[c] = ||BY_c||^2.  nsides blocks of
 // partials (each nparts x ne*m) and of bynorm2 (each m) are checked together.

@@ -137,6 +137,35 @@ template int launch_multishift_residual<float>(const CsrView &, const CsrView *,
 // over the per-CTA partials in fixed order; the maximum is folded in with an
 // integer atomicMax on the bits of the (non-negative) double, which is
 // order-independent.
+// Same product with the grid capped at max_grid CTAs, so that the partial
+// sums fit a caller-provided buffer of max_grid * ne * m doubles.
+template <typename Tout>
+int launch_multishift_residual_capped(const CsrView &A, const CsrView *B, int ne, const cxd *d_z, const cxd *d_w,
+                                      const cxd *X, const cxd *BY, cx<Tout> *R, cxd *Q, double *partial, int m,
+                                      int max_grid, cudaStream_t s) {
+  int grid = ms_grid(A.n);
+  if (grid > max_grid) grid = max_grid;
+  const int rpc = ceil_div(A.n, grid);
+  const int g = ceil_div(A.n, rpc);
+  const size_t xns = (size_t)A.n * m;
+  CsrView Bv = B ? *B : A;
+  const bool bc = B ? B->cplx : false;
+#define MS_LAUNCH(AC, BC)                                                                                \
+  k_multishift_residual<Tout, AC, BC><<<g, kMsThreads, 0, s>>>(A, Bv, B != nullptr, ne, d_z, d_w, X, xns, \
+                                                               BY, R, Q, partial, m, rpc, nullptr)
+  if (A.cplx) {
+    if (bc) MS_LAUNCH(true, true); else MS_LAUNCH(true, false);
+  } else {
+    if (bc) MS_LAUNCH(false, true); else MS_LAUNCH(false, false);
+  }
+#undef MS_LAUNCH
+  note_launch();
+  return g;
+}
+template int launch_multishift_residual_capped<double>(const CsrView &, const CsrView *, int, const cxd *,
+                                                       const cxd *, const cxd *, const cxd *, cxd *, cxd *, double *,
+                                                       int, int, cudaStream_t);
+
 __global__ void k_residual_rel(const double *partial, int nparts, int P, int m, const double *bynorm2, int nsides,
                                unsigned long long *maxbits) {
   __shared__ double red[128];

@@ -53,7 +53,7 @@ class Info(C.Structure):
 
 EXPORTS = ["feast_nh_default_opts", "feast_nh_init", "feast_nh_filter", "feast_nh_rr", "feast_nh_solve",
            "feast_nh_destroy", "feast_nh_strerror", "feast_nh_last_error", "feast_nh_nodes",
-           "feast_nh_multishift_residual", "feast_nh_kernel_launches"]
+           "feast_nh_multishift_residual", "feast_nh_kernel_launches", "feast_nh_multishift_residual_noalloc"]
 
 _lib = None
 
@@ -82,6 +82,9 @@ def lib():
     L.feast_nh_last_error.restype = C.c_char_p
     L.feast_nh_nodes.argtypes = [C.POINTER(ContourS), C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.feast_nh_multishift_residual.argtypes = [vp, vp, vp, vp, vp, i32]
+    L.feast_nh_multishift_residual_noalloc.argtypes = [C.POINTER(Csr), C.POINTER(Csr), C.POINTER(ContourS), vp, vp,
+                                                       vp, vp, vp, i32, vp]
+    L.feast_nh_multishift_residual_noalloc.restype = i32
     L.feast_nh_kernel_launches.argtypes = []
     L.feast_nh_kernel_launches.restype = C.c_uint64
     for f in ("feast_nh_init", "feast_nh_filter", "feast_nh_rr", "feast_nh_solve", "feast_nh_nodes",
@@ -127,6 +130,26 @@ def contour_struct(con) -> tuple[ContourS, list]:
 def kernel_launches() -> int:
     """Kernels libfeast_nh.so has launched in this process."""
     return int(lib().feast_nh_kernel_launches())
+
+
+def multishift_residual_noalloc(A_dev, B_dev, contour, X, BY, want_q=True, stream=None):
+    """feast_nh_multishift_residual_noalloc: R, Q and relative column norms
+    with no context and no device allocation inside the library (the output
+    tensors are allocated here by the caller)."""
+    ne, n, m = X.shape
+    R = torch.empty_like(X)
+    Q = torch.empty((n, m), dtype=torch.complex128, device=X.device) if want_q else None
+    rel = torch.empty(ne * m, dtype=torch.float64, device=X.device)
+    cs, keep = contour_struct(contour)
+    a = _csr_struct(A_dev)
+    b = _csr_struct(B_dev) if B_dev is not None else None
+    st = stream if stream is not None else torch.cuda.current_stream(X.device)
+    rc = lib().feast_nh_multishift_residual_noalloc(C.byref(a), C.byref(b) if b is not None else None, C.byref(cs),
+                                                    _ptr(X.contiguous()), _ptr(BY.contiguous()), _ptr(R), _ptr(Q),
+                                                    _ptr(rel), m, C.c_void_p(st.cuda_stream))
+    if rc != OK:
+        raise FeastError(rc, "feast_nh_multishift_residual_noalloc")
+    return R, Q, rel.view(ne, m)
 
 
 def nodes(con):
