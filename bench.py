@@ -260,6 +260,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "spmm": spmm, "kernel_ms_per_step": kernel_times,
         "cpu_baseline": cpu, "clocks": clocks, "plain_fp64": plain,
         "check": {"m": int(ms_found[-1]), "iterations": inf["iterations"], "max_res": max_res,
+                  "inner_steps_last_filter": inf["inner_steps"], "inner_res": inf["inner_res"],
                   "max_rel_eig_err_vs_closed_form": eig_err},
     }
     return line

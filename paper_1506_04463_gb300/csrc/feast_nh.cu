@@ -257,25 +257,31 @@ void do_filter(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, cxd *Q, cxd *Qh, 
     for (int it = 0; it < steps; ++it) {
       int kr = ev_begin(ctx, ctx->ev_resid);
       const int gm = launch_multishift_residual<float>(ctx->A, Bp, ne, ctx->dz, ctx->dw, ctx->Xn, BY, (cxf *)ctx->Rn,
-                                                       Q, ctx->part, m, ctx->d_done, ctx->s);
+                                                       Q, ctx->part, m, nullptr, ctx->s);
       ev_end(ctx, ctx->ev_resid, kr);
       if (!cs) {
         kr = ev_begin(ctx, ctx->ev_resid);
         launch_multishift_residual<float>(ctx->AH, BHp, ne, ctx->dzc, ctx->dwc, ctx->Xhn, BhYh, (cxf *)ctx->Rhn, Qh,
-                                          ctx->part + (size_t)gm * ne * m, m, ctx->d_done, ctx->s);
+                                          ctx->part + (size_t)gm * ne * m, m, nullptr, ctx->s);
         ev_end(ctx, ctx->ev_resid, kr);
       }
       launch_residual_check(ctx->part, gm, ne, m, ctx->bynorm2, cs ? 1 : 2, ctx->o.inner_tol, ctx->d_maxrel,
                             ctx->d_done, ctx->s);
+      // one 4-byte read per refinement step decides whether to go on
+      CKC(cudaMemcpyAsync(ctx->h_small + 2, ctx->d_done, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+      CKC(cudaStreamSynchronize(ctx->s));
+      int done = 0;
+      std::memcpy(&done, ctx->h_small + 2, sizeof(int));
+      ctx->inner_steps = it + 1;
+      if (done) break;
       if (it + 1 < steps) {
         int ks = ev_begin(ctx, ctx->ev_solve);
         CKC(band_solve_sides<float, float>(n, ctx->kl, ctx->ku, ne, (const cxf *)ctx->band, (const cxf *)ctx->Rn,
                                            cs ? nullptr : (const cxf *)ctx->Rhn, xns, m, ctx->Xn,
-                                           cs ? nullptr : ctx->Xhn, xns, 1, (cxf *)ctx->ysc, ctx->d_done, ctx->s));
+                                           cs ? nullptr : ctx->Xhn, xns, 1, (cxf *)ctx->ysc, nullptr, ctx->s));
         ev_end(ctx, ctx->ev_solve, ks);
       }
     }
-    ctx->inner_steps = steps;
   }
   if (cs) launch_copy_conj(Q, Qh, (size_t)n * m, ctx->s);
   check_launch(ctx, "contour integration");
