@@ -12,6 +12,7 @@
 // Storage (per node, row-major band): row r, offset t in [0, W), W = kl+ku+1,
 // holds entry (r, r-kl+t); after factorisation t < kl holds L (unit lower) and
 // t >= kl holds U.
+#include <cooperative_groups.h>
 #include <type_traits>
 #include "kernels.h"
 
@@ -174,6 +175,32 @@ __global__ void __launch_bounds__(256) k_band_panel(int n, int kl, int ku, int k
   }
 }
 
+// Register panel elimination with compile-time column indices: thread i holds
+// row i of the panel in row[]; prow_s is a double-buffered pivot row.
+template <typename T, int NB>
+__device__ __forceinline__ void panel_eliminate(cx<T> (&row)[NB], cx<T> (*prow_s)[NB], int i, bool own, int nb,
+                                                int kl, int *err) {
+#pragma unroll
+  for (int p = 0; p < NB; ++p) {
+    if (p < nb) {
+      cx<T> *pr = prow_s[p & 1];
+      if (i == p) {
+#pragma unroll
+        for (int q = p; q < NB; ++q) pr[q] = row[q];
+      }
+      __syncthreads();
+      if (own && i > p && i - p <= kl) {
+        const cx<T> piv = pr[p];
+        if (piv.re == 0 && piv.im == 0) atomicOr(err, DEVERR_ZERO_PIVOT);
+        const cx<T> l = cdiv(row[p], piv);
+        row[p] = l;
+#pragma unroll
+        for (int q = p + 1; q < NB; ++q) cfms(row[q], l, pr[q]);
+      }
+    }
+  }
+}
+
 // Register form of the panel step for bands with NB + kl <= 512: thread i
 // holds row k+i of the panel (columns [k, k+nb)) in registers; the pivot row
 // of each elimination step is published through a double-buffered shared
@@ -194,27 +221,7 @@ __global__ void __launch_bounds__(512) k_band_panel_reg(int n, int kl, int ku, i
     const int d = q - i;
     row[q] = (own && q < nb && d >= -kl && d <= ku) ? Bd[(size_t)(k + i) * W + (d + kl)] : mk<T>(0, 0);
   }
-  for (int p = 0; p < nb; ++p) {
-    cx<T> *pr = prow_s[p & 1];
-    if (i == p) {
-#pragma unroll
-      for (int q = 0; q < NB; ++q) pr[q] = row[q];
-    }
-    __syncthreads();
-    if (own && i > p && i - p <= kl) {
-      const cx<T> piv = pr[p];
-      if (piv.re == 0 && piv.im == 0) atomicOr(err, DEVERR_ZERO_PIVOT);
-      cx<T> l;
-#pragma unroll
-      for (int q = 0; q < NB; ++q)
-        if (q == p) l = cdiv(row[q], piv);
-#pragma unroll
-      for (int q = 0; q < NB; ++q) {
-        if (q == p) row[q] = l;
-        if (q > p) cfms(row[q], l, pr[q]);
-      }
-    }
-  }
+  panel_eliminate<T, NB>(row, prow_s, i, own, nb, kl, err);
   if (own) {
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
@@ -317,6 +324,168 @@ __global__ void __launch_bounds__(256) k_band_update(int n, int kl, int ku, int 
   }
 }
 
+// ---------------------------------------------------------------------------
+// factorisation as one persistent launch: one thread-block cluster of FCL CTAs
+// per node.  Step k (columns [k, k+nb)): the CTA owning the panel factors it
+// in registers (thread = row); cluster barrier; every CTA forms U12 for the
+// 16-column groups it owns (group g belongs to CTA g mod FCL) and applies
+// the rank-nb update to its columns of the trailing window; cluster barrier.
+// Band data shared between CTAs is read with ld.global.cg (L2), so no CTA can
+// see a stale L1 line.  Requires nb + kl <= 512 and ku <= 480.
+// ---------------------------------------------------------------------------
+constexpr int FCL = 8;       // CTAs per cluster
+constexpr int FNT = 512;     // threads per CTA
+constexpr int FGW = 16;      // column-group width
+constexpr int FMAXC = 64;    // columns a CTA owns per step (ku <= 480)
+constexpr int FRC = 64;      // rows of L21 staged per chunk
+
+template <typename T>
+__device__ __forceinline__ cx<T> ldcg(const cx<T> *p) {
+  if constexpr (sizeof(T) == 4) {
+    float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+    return mk<T>(v.x, v.y);
+  } else {
+    double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
+    return mk<T>(v.x, v.y);
+  }
+}
+
+template <typename T, int NB>
+__global__ void __cluster_dims__(FCL, 1, 1) __launch_bounds__(FNT)
+    k_band_factor_cluster(int n, int kl, int ku, cx<T> *band, size_t ns, int *err) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T> *Ls = reinterpret_cast<cx<T> *>(smem_raw);  // kl x NB: L21 of the current step
+  __shared__ cx<T> prow_s[2][NB];
+  __shared__ cx<T> L11[NB][NB + 1];
+  __shared__ cx<T> Us[NB][FMAXC];
+  __shared__ int mycol[FMAXC];
+  __shared__ int nmy_s;
+  const int W = kl + ku + 1;
+  cx<T> *Bd = band + (size_t)blockIdx.y * ns;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int k = 0; k < n; k += NB) {
+    const int nb = min(NB, n - k);
+    const int owner = (k / NB) % FCL;
+    // ---------------- panel (owner CTA) ----------------
+    if (rank == owner) {
+      const int prow = min(n - k, nb + kl);
+      const int i = tid;
+      const bool own = i < prow;
+      cx<T> row[NB];
+#pragma unroll
+      for (int q = 0; q < NB; ++q) {
+        const int d = q - i;
+        row[q] = (own && q < nb && d >= -kl && d <= ku) ? ldcg(Bd + (size_t)(k + i) * W + (d + kl)) : mk<T>(0, 0);
+      }
+      panel_eliminate<T, NB>(row, prow_s, i, own, nb, kl, err);
+      if (own) {
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+          const int d = q - i;
+          if (q < nb && d >= -kl && d <= ku) Bd[(size_t)(k + i) * W + (d + kl)] = row[q];
+        }
+      }
+    }
+    cluster.sync();
+    // ---------------- U12 and trailing update (all CTAs) ----------------
+    const int c_beg = k + nb, c_end = min(n, k + nb + ku), r_end = min(n, k + nb + kl);
+    const int nrows = r_end - c_beg;
+    if (c_beg < c_end && nrows > 0) {
+      // owned columns: slot t -> group g0 + 8*(t/16), column 16g + t%16 (or -1)
+      if (tid < FMAXC) {
+        int g0 = c_beg / FGW;
+        g0 += ((rank - g0) % FCL + FCL) % FCL;
+        const int c = (g0 + FCL * (tid / FGW)) * FGW + tid % FGW;
+        mycol[tid] = (c >= c_beg && c < c_end) ? c : -1;
+      }
+      for (int e = tid; e < NB * NB; e += FNT) {
+        const int r = e / NB, p = e - r * NB;
+        L11[r][p] = (r < nb && p < r && r - p <= kl) ? ldcg(Bd + (size_t)(k + r) * W + (p - r + kl)) : mk<T>(0, 0);
+      }
+      for (int e = tid; e < nrows * NB; e += FNT) {
+        const int rr = e / NB, p = e - rr * NB;
+        const int r = c_beg + rr;
+        Ls[e] = (p < nb && r - (k + p) <= kl) ? ldcg(Bd + (size_t)r * W + (k + p - r + kl)) : mk<T>(0, 0);
+      }
+      __syncthreads();
+      // U12 = L11^{-1} A12, one owned column per thread
+      if (tid < FMAXC && mycol[tid] >= 0) {
+        const int c = mycol[tid];
+        cx<T> u[NB];
+#pragma unroll
+        for (int r = 0; r < NB; ++r) {
+          const int d = c - (k + r);
+          u[r] = (r < nb && d <= ku) ? ldcg(Bd + (size_t)(k + r) * W + (d + kl)) : mk<T>(0, 0);
+        }
+#pragma unroll
+        for (int r = 1; r < NB; ++r)
+#pragma unroll
+          for (int p = 0; p < r; ++p) cfms(u[r], L11[r][p], u[p]);
+#pragma unroll
+        for (int r = 0; r < NB; ++r) {
+          const int d = c - (k + r);
+          if (r < nb && d <= ku) Bd[(size_t)(k + r) * W + (d + kl)] = u[r];
+          Us[r][tid] = u[r];
+        }
+      }
+      __syncthreads();
+      // A22 -= L21 U12: warp pair per 64 owned slots, 8 row chunks; lanes on
+      // consecutive owned columns (coalesced along band rows), U12 column in
+      // registers, L21 entries as shared-memory broadcasts, 4 rows at a time
+      // with the next 4 entries loaded ahead.
+      const int j = (warp & 1) * 32 + lane;
+      const int chunk = warp >> 1;
+      const int c = mycol[j];
+      if (c >= 0) {
+        cx<T> u[NB];
+#pragma unroll
+        for (int p = 0; p < NB; ++p) u[p] = Us[p][j];
+        constexpr int NCH = FNT / 64;
+        const int per = ((nrows + NCH - 1) / NCH + 3) & ~3;
+        const int rb = chunk * per, re = min(nrows, rb + per);
+        cx<T> cur[4], nxt[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int rr = rb + q;
+          nxt[q] = rr < re ? ldcg(Bd + (size_t)(c_beg + rr) * W + (c - (c_beg + rr) + kl)) : mk<T>(0, 0);
+        }
+        for (int r4 = rb; r4 < re; r4 += 4) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) cur[q] = nxt[q];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int rr = r4 + 4 + q;
+            nxt[q] = rr < re ? ldcg(Bd + (size_t)(c_beg + rr) * W + (c - (c_beg + rr) + kl)) : mk<T>(0, 0);
+          }
+#pragma unroll
+          for (int p = 0; p < NB; ++p) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int rr = min(r4 + q, nrows - 1);
+              cfms(cur[q], Ls[rr * NB + p], u[p]);
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int rr = r4 + q;
+            if (rr < re) Bd[(size_t)(c_beg + rr) * W + (c - (c_beg + rr) + kl)] = cur[q];
+          }
+        }
+      }
+    }
+    cluster.sync();
+  }
+}
+
+// The FP64 factorisation is bound by the FP64 pipes; the per-step launches
+// spread its trailing updates over every SM, which measured faster there.
+template <typename T> bool band_factor_cluster_ok(int kl, int ku) {
+  return sizeof(T) == 4 && FactorCfg<T>::NB + kl <= FNT && ku <= (FMAXC / FGW) * FGW * FCL - 2 * FGW;
+}
+
 template <typename T> bool band_fits(int kl, int ku) {
   constexpr int NB = FactorCfg<T>::NB;
   return panel_smem<T>(kl, ku, NB) <= 220 * 1024;
@@ -328,6 +497,23 @@ template <typename T>
 cudaError_t band_factor(int n, int kl, int ku, int ne, cx<T> *band, int *d_err, cudaStream_t s) {
   constexpr int NB = FactorCfg<T>::NB;
   const size_t ns = (size_t)n * (kl + ku + 1);
+  static int cluster_fits = -1;  // can one FCL-CTA cluster be resident at all?
+  const size_t fsmem = (size_t)kl * NB * sizeof(cx<T>);
+  if (cluster_fits < 0) {
+    cudaFuncSetAttribute(k_band_factor_cluster<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(FCL, 1, 1);
+    cfg.blockDim = dim3(FNT, 1, 1);
+    cfg.dynamicSmemBytes = 160 * 1024;
+    int nc = 0;
+    cluster_fits = (cudaOccupancyMaxActiveClusters(&nc, k_band_factor_cluster<T, NB>, &cfg) == cudaSuccess && nc > 0);
+    cudaGetLastError();
+  }
+  if (cluster_fits && band_factor_cluster_ok<T>(kl, ku) && fsmem <= 160 * 1024) {
+    k_band_factor_cluster<T, NB><<<dim3(FCL, ne), FNT, fsmem, s>>>(n, kl, ku, band, ns, d_err);
+    note_launch();
+    return cudaGetLastError();
+  }
   const size_t smem = panel_smem<T>(kl, ku, NB);
   const bool reg = NB + kl <= 512;
   const int reg_threads = ceil_div(NB + kl, 32) * 32;
@@ -560,6 +746,72 @@ __global__ void __launch_bounds__(R *NB / RPT) k_band_solve(int n, int kl, int k
   }
 }
 
+// Inverses of the 16 x 16 diagonal blocks of L (unit lower) and U (upper) of
+// every node's factors, so that the triangular solves finish each 16-row
+// block with a dense product instead of a sequential substitution.  One warp
+// per block: lanes 0..15 form column j of L11^{-1}, lanes 16..31 column j of
+// U11^{-1}.  Output per (node, block): [L^{-1} | U^{-1}], each row-major.
+constexpr int DIB = 16;
+template <typename T>
+__device__ __forceinline__ cx<T> band_ld(const cx<T> *B, size_t o) { return B[o]; }
+template <typename T>
+__global__ void __launch_bounds__(256) k_band_diag_inv(int n, int kl, int ku, const cx<T> *band, size_t ns,
+                                                       cx<T> *dinv) {
+  __shared__ cx<T> Lb[8][DIB][DIB + 1];
+  __shared__ cx<T> Ub[8][DIB][DIB + 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nblk = ceil_div(n, DIB);
+  const int b = blockIdx.x * 8 + warp;
+  const int node = blockIdx.y;
+  if (b >= nblk) return;
+  const int W = kl + ku + 1;
+  const cx<T> *Bd = band + (size_t)node * ns;
+  const int kb = b * DIB, nbk = min(DIB, n - kb);
+  for (int e = lane; e < DIB * DIB; e += 32) {
+    const int r = e / DIB, c = e % DIB;
+    cx<T> lv = mk<T>(r == c ? 1 : 0, 0), uv = mk<T>(r == c ? 1 : 0, 0);
+    if (r < nbk && c < nbk) {
+      const int d = c - r;
+      if (d < 0 && -d <= kl) lv = band_ld(Bd, (size_t)(kb + r) * W + (d + kl));
+      if (d >= 0 && d <= ku) uv = band_ld(Bd, (size_t)(kb + r) * W + (d + kl));
+    }
+    Lb[warp][r][c] = lv;
+    Ub[warp][r][c] = uv;
+  }
+  __syncwarp();
+  const int j = lane & 15;
+  cx<T> x[DIB];
+  if (lane < 16) {
+#pragma unroll
+    for (int i = 0; i < DIB; ++i) {
+      cx<T> v = mk<T>(i == j ? 1 : 0, 0);
+#pragma unroll
+      for (int p = 0; p < i; ++p) cfms(v, Lb[warp][i][p], x[p]);
+      x[i] = v;
+    }
+  } else {
+#pragma unroll
+    for (int i = DIB - 1; i >= 0; --i) {
+      cx<T> v = mk<T>(i == j ? 1 : 0, 0);
+#pragma unroll
+      for (int p = i + 1; p < DIB; ++p) cfms(v, Ub[warp][i][p], x[p]);
+      x[i] = cdiv(v, Ub[warp][i][i]);
+    }
+  }
+  cx<T> *out = dinv + ((size_t)node * nblk + b) * (2 * DIB * DIB) + (lane < 16 ? 0 : DIB * DIB);
+#pragma unroll
+  for (int i = 0; i < DIB; ++i) out[i * DIB + j] = x[i];
+}
+
+template <typename T>
+void launch_band_diag_inv(int n, int kl, int ku, int ne, const cx<T> *band, cx<T> *dinv, cudaStream_t s) {
+  const int nblk = ceil_div(n, DIB);
+  k_band_diag_inv<T><<<dim3(ceil_div(nblk, 8), ne), 256, 0, s>>>(n, kl, ku, band, (size_t)n * (kl + ku + 1), dinv);
+  note_launch();
+}
+template void launch_band_diag_inv<float>(int, int, int, int, const cxf *, cxf *, cudaStream_t);
+size_t band_diag_inv_elems(int n, int ne) { return (size_t)ne * ceil_div(n, DIB) * 2 * DIB * DIB; }
+
 // FP32 variant.  The band range of each row block is split across the 8 warps
 // of the CTA; each lane keeps a 2 x 4 register tile (rows rl+8q, columns
 // cl+4t).  The factor tile of the next block is fetched with cp.async into a
@@ -569,8 +821,9 @@ __global__ void __launch_bounds__(R *NB / RPT) k_band_solve(int n, int kl, int k
 // warp owns 2 of the R = 16 columns, one row per lane; rows are finalised in
 // order and broadcast with shuffles).
 namespace ks {
-constexpr int NB = 16, R = 16, WARPS = 8, NT = 32 * WARPS;
+constexpr int NB = 16, R = 16, WARPS = 16, NT = 32 * WARPS;
 constexpr int RED_LD = R + 1;
+constexpr int DLD = NB + 1;  // padded row stride of the diagonal-block inverse tile
 __host__ __device__ inline int tw_pad(int bw) { return (bw + NB) | 1; }
 __host__ __device__ inline int ring_rows(int bw) { return ceil_div(bw + NB, NB) * NB; }
 }  // namespace ks
@@ -591,8 +844,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 //          bwd tile (r, i) = L(i, r)^*, i in (r, r+kl];  diag 1
 // (conjugation is applied when the tile is read)
 template <bool HERM>
-__device__ __forceinline__ void ks_fetch(const cxf *Bd, int n, int kl, int ku, int W, int nblk, int step, cxf *Mb,
-                                         cxf *db, int TWP) {
+__device__ __forceinline__ void ks_fetch(const cxf *Bd, const cxf *Dv, int n, int kl, int ku, int W, int nblk,
+                                         int step, cxf *Mb, cxf *db, int TWP) {
   using namespace ks;
   const bool fwd = step < nblk;
   const int b = fwd ? step : 2 * nblk - 1 - step;
@@ -616,17 +869,19 @@ __device__ __forceinline__ void ks_fetch(const cxf *Bd, int n, int kl, int ku, i
     if (ok) src = HERM ? Bd + (size_t)i * W + (r - i + kl) : Bd + (size_t)r * W + (i - r + kl);
     cp_async8(Mb + rr * TWP + ii, src, ok);
   }
-  if (threadIdx.x < NB) {
-    const int rr = threadIdx.x;
-    const bool ok = rr < nbk && (HERM ? fwd : !fwd);
-    cp_async8(db + rr, ok ? Bd + (size_t)(kb + rr) * W + kl : Bd, ok);
+  // inverse of the diagonal block: L11^{-1} for N-forward / H-backward,
+  // U11^{-1} for N-backward / H-forward (the H sides use its conjugate transpose)
+  {
+    const bool useL = fwd != HERM;
+    const cxf *src = Dv + (size_t)b * (2 * NB * NB) + (useL ? 0 : NB * NB);
+    for (int e = threadIdx.x; e < NB * NB; e += NT) cp_async8(db + (e / NB) * DLD + e % NB, src + e, true);
   }
   cp_async_commit();
 }
 
 template <bool HERM, typename Tin>
-__device__ __forceinline__ void ks_body(int n, int kl, int ku, const cxf *Bd, const cx<Tin> *Rh, cxd *Xn, cxf *Ys,
-                                        int m, int mode, int c0, unsigned char *smem_raw) {
+__device__ __forceinline__ void ks_body(int n, int kl, int ku, const cxf *Bd, const cxf *Dv, const cx<Tin> *Rh,
+                                        cxd *Xn, cxf *Ys, int m, int mode, int c0, unsigned char *smem_raw) {
   using namespace ks;
   const int W = kl + ku + 1;
   const int bwmax = max(kl, ku);
@@ -635,17 +890,18 @@ __device__ __forceinline__ void ks_body(int n, int kl, int ku, const cxf *Bd, co
   cxf *Mbuf = reinterpret_cast<cxf *>(smem_raw);      // 2 x NB x TWP
   cxf *ring = Mbuf + (size_t)2 * NB * TWP;             // RB x R
   cxf *red = ring + (size_t)RB * R;                    // WARPS x NB x RED_LD
-  cxf *dbuf = red + (size_t)WARPS * NB * RED_LD;       // 2 x NB
+  cxf *dbuf = red + (size_t)WARPS * NB * RED_LD;       // 2 x NB x DLD (diagonal-block inverse)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int rl = lane >> 2, cl = lane & 3;
-  const int tc = 2 * warp + (lane >> 4), tr = lane & 15;
+  const bool owner = warp < R / 2;  // warps that own two columns each for the in-block solve
+  const int tc = 2 * (warp % (R / 2)) + (lane >> 4), tr = lane & 15;
   const int gc = c0 + tc;
-  const bool cok = gc < m;
+  const bool cok = owner && gc < m;
   const int nblk = ceil_div(n, NB);
   const int nsteps = 2 * nblk;
   const unsigned full = 0xffffffffu;
 
-  ks_fetch<HERM>(Bd, n, kl, ku, W, nblk, 0, Mbuf, dbuf, TWP);
+  ks_fetch<HERM>(Bd, Dv, n, kl, ku, W, nblk, 0, Mbuf, dbuf, TWP);
   for (int step = 0; step < nsteps; ++step) {
     const bool fwd = step < nblk;
     const int b = fwd ? step : 2 * nblk - 1 - step;
@@ -654,7 +910,7 @@ __device__ __forceinline__ void ks_body(int n, int kl, int ku, const cxf *Bd, co
     const int bw = fwd ? (HERM ? ku : kl) : (HERM ? kl : ku);
     const int ibase = fwd ? kb - bw : kb;
     cxf *Ms = Mbuf + (size_t)(step & 1) * NB * TWP;
-    cxf *dg = dbuf + (step & 1) * NB;
+    cxf *dg = dbuf + (size_t)(step & 1) * NB * DLD;
     // right-hand side of the row this lane finalises
     cxf acc2 = mk(0.f, 0.f);
     {
@@ -664,8 +920,8 @@ __device__ __forceinline__ void ks_body(int n, int kl, int ku, const cxf *Bd, co
     cp_async_wait_all();
     __syncthreads();
     if (step + 1 < nsteps)
-      ks_fetch<HERM>(Bd, n, kl, ku, W, nblk, step + 1, Mbuf + (size_t)((step + 1) & 1) * NB * TWP,
-                     dbuf + ((step + 1) & 1) * NB, TWP);
+      ks_fetch<HERM>(Bd, Dv, n, kl, ku, W, nblk, step + 1, Mbuf + (size_t)((step + 1) & 1) * NB * TWP,
+                     dbuf + (size_t)((step + 1) & 1) * NB * DLD, TWP);
     // ---- GEMM over the rows already solved, split over warps ----
     int hlo, hhi;
     if (fwd) {
@@ -685,7 +941,7 @@ __device__ __forceinline__ void ks_body(int n, int kl, int ku, const cxf *Bd, co
       for (int t = 0; t < 4; ++t) acc[q][t] = mk(0.f, 0.f);
     if (wlo < whi) {
       int slot = wlo % RB;
-#pragma unroll 2
+#pragma unroll 4
       for (int i = wlo; i < whi; ++i) {
         cxf mv[2], yv[4];
         const int col = i - ibase;
@@ -708,53 +964,33 @@ __device__ __forceinline__ void ks_body(int n, int kl, int ku, const cxf *Bd, co
 #pragma unroll
       for (int t = 0; t < 4; ++t) red[(warp * NB + rl + 8 * q) * RED_LD + cl + 4 * t] = acc[q][t];
     __syncthreads();
-    {
+    if (owner) {
       cxf sum = mk(0.f, 0.f);
 #pragma unroll
       for (int w = 0; w < WARPS; ++w) sum = sum + red[(w * NB + tr) * RED_LD + tc];
       acc2 = acc2 - sum;
     }
-    // ---- warp-local triangle: lane (tc, tr) owns row tr of column tc ----
-    const bool divide = HERM ? fwd : !fwd;
-    if (fwd) {
-      for (int p = 0; p < nbk; ++p) {
-        const int src = (lane & 16) | p;
-        cxf x = acc2;
-        if (divide) {
-          cxf d = dg[p];
-          if (HERM) d.im = -d.im;
-          x = cdiv(x, d);
+    // ---- in-block solve: x = D acc with D the inverse of the diagonal block ----
+    if (owner) {
+      cxf x = mk(0.f, 0.f);
+#pragma unroll
+      for (int p = 0; p < NB; ++p) {
+        cxf a;
+        a.re = __shfl_sync(full, acc2.re, (lane & 16) | p);
+        a.im = __shfl_sync(full, acc2.im, (lane & 16) | p);
+        cxf dv;
+        if (HERM) {
+          dv = dg[p * DLD + tr];
+          dv.im = -dv.im;
+        } else {
+          dv = dg[tr * DLD + p];
         }
-        x.re = __shfl_sync(full, x.re, src);
-        x.im = __shfl_sync(full, x.im, src);
-        if (tr == p) acc2 = x;
-        if (tr > p) {
-          cxf mv = Ms[tr * TWP + bw + p];
-          if (HERM) mv.im = -mv.im;
-          cfms(acc2, mv, x);
-        }
+        cfma(x, dv, a);
       }
-    } else {
-      for (int p = nbk - 1; p >= 0; --p) {
-        const int src = (lane & 16) | p;
-        cxf x = acc2;
-        if (divide) {
-          cxf d = dg[p];
-          if (HERM) d.im = -d.im;
-          x = cdiv(x, d);
-        }
-        x.re = __shfl_sync(full, x.re, src);
-        x.im = __shfl_sync(full, x.im, src);
-        if (tr == p) acc2 = x;
-        if (tr < p) {
-          cxf mv = Ms[tr * TWP + p];
-          if (HERM) mv.im = -mv.im;
-          cfms(acc2, mv, x);
-        }
-      }
+      acc2 = x;
     }
     // ---- publish the block's solution ----
-    if (tr < nbk) {
+    if (owner && tr < nbk) {
       const int r = kb + tr;
       ring[(r % RB) * R + tc] = acc2;
       if (fwd) {
@@ -771,8 +1007,8 @@ __device__ __forceinline__ void ks_body(int n, int kl, int ku, const cxf *Bd, co
 
 template <typename Tin>
 __global__ void __launch_bounds__(ks::NT) k_band_solve_ks(int n, int kl, int ku, const cxf *band, size_t bns,
-                                                          SolveSides io, size_t rns, int m, size_t xns, int mode,
-                                                          cxf *ysc, const int *skip) {
+                                                          const cxf *dinv, SolveSides io, size_t rns, int m,
+                                                          size_t xns, int mode, cxf *ysc, const int *skip) {
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int side = blockIdx.z;
@@ -782,16 +1018,17 @@ __global__ void __launch_bounds__(ks::NT) k_band_solve_ks(int n, int kl, int ku,
   const cx<Tin> *Rh = reinterpret_cast<const cx<Tin> *>(side ? io.rhs[1] : io.rhs[0]) + (size_t)node * rns;
   cxd *Xn = (side ? io.X[1] : io.X[0]) + (size_t)node * xns;
   cxf *Ys = ysc + (((size_t)side * gridDim.y + node) * gridDim.x + blockIdx.x) * (size_t)n * ks::R;
+  const cxf *Dv = dinv + (size_t)node * ceil_div(n, ks::NB) * (2 * ks::NB * ks::NB);
   if (side)
-    ks_body<true, Tin>(n, kl, ku, Bd, Rh, Xn, Ys, m, mode, c0, smem_raw);
+    ks_body<true, Tin>(n, kl, ku, Bd, Dv, Rh, Xn, Ys, m, mode, c0, smem_raw);
   else
-    ks_body<false, Tin>(n, kl, ku, Bd, Rh, Xn, Ys, m, mode, c0, smem_raw);
+    ks_body<false, Tin>(n, kl, ku, Bd, Dv, Rh, Xn, Ys, m, mode, c0, smem_raw);
 }
 
 static size_t solve_smem_ks(int kl, int ku) {
   const int bwmax = kl > ku ? kl : ku;
   return ((size_t)2 * ks::NB * ks::tw_pad(bwmax) + (size_t)ks::ring_rows(bwmax) * ks::R +
-          (size_t)ks::WARPS * ks::NB * ks::RED_LD + 2 * ks::NB) * sizeof(cxf);
+          (size_t)ks::WARPS * ks::NB * ks::RED_LD + 2 * ks::NB * ks::DLD) * sizeof(cxf);
 }
 
 template <typename T>
@@ -806,7 +1043,7 @@ static size_t solve_smem(int kl, int ku) {
 // rhs/X pointers for the two sides are packed by the caller through the
 // globals below (set by band_solve_sides).
 template <typename T, typename Tin>
-cudaError_t band_solve_sides(int n, int kl, int ku, int ne, const cx<T> *band, const cx<Tin> *rhsR,
+cudaError_t band_solve_sides(int n, int kl, int ku, int ne, const cx<T> *band, const cx<T> *dinv, const cx<Tin> *rhsR,
                              const cx<Tin> *rhsL, size_t rns, int m, cxd *XR, cxd *XL, size_t xns, int mode,
                              cx<T> *ysc, const int *skip, cudaStream_t s) {
   SolveSides io;
@@ -822,7 +1059,7 @@ cudaError_t band_solve_sides(int n, int kl, int ku, int ne, const cx<T> *band, c
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid(ceil_div(m, ks::R), ne, nsides);
-    kern<<<grid, ks::NT, smem, s>>>(n, kl, ku, band, bns, io, rns, m, xns, mode, ysc, skip);
+    kern<<<grid, ks::NT, smem, s>>>(n, kl, ku, band, bns, dinv, io, rns, m, xns, mode, ysc, skip);
     note_launch();
   } else {
     constexpr int NB = SolveCfg<T>::NB, R = SolveCfg<T>::R, RPT = SolveCfg<T>::RPT;
@@ -837,13 +1074,13 @@ cudaError_t band_solve_sides(int n, int kl, int ku, int ne, const cx<T> *band, c
   }
   return cudaGetLastError();
 }
-template cudaError_t band_solve_sides<float, float>(int, int, int, int, const cxf *, const cxf *, const cxf *,
+template cudaError_t band_solve_sides<float, float>(int, int, int, int, const cxf *, const cxf *, const cxf *, const cxf *,
                                                     size_t, int, cxd *, cxd *, size_t, int, cxf *, const int *,
                                                     cudaStream_t);
-template cudaError_t band_solve_sides<float, double>(int, int, int, int, const cxf *, const cxd *, const cxd *,
+template cudaError_t band_solve_sides<float, double>(int, int, int, int, const cxf *, const cxf *, const cxd *, const cxd *,
                                                      size_t, int, cxd *, cxd *, size_t, int, cxf *, const int *,
                                                      cudaStream_t);
-template cudaError_t band_solve_sides<double, double>(int, int, int, int, const cxd *, const cxd *, const cxd *,
+template cudaError_t band_solve_sides<double, double>(int, int, int, int, const cxd *, const cxd *, const cxd *, const cxd *,
                                                       size_t, int, cxd *, cxd *, size_t, int, cxd *, const int *,
                                                       cudaStream_t);
 

@@ -40,6 +40,7 @@ struct feast_nh_ctx {
   bool factored = false;
   void *band = nullptr;
   void *ysc = nullptr;
+  void *dinv = nullptr;
   cxd *Yw = nullptr, *Yhw = nullptr, *Qw = nullptr, *Qhw = nullptr, *Uw = nullptr, *Uhw = nullptr, *T1 = nullptr,
       *T2 = nullptr, *BYw = nullptr, *BhYw = nullptr;
   cxd *Xn = nullptr, *Xhn = nullptr;
@@ -195,6 +196,7 @@ void factorize(feast_nh_ctx *ctx) {
   if (fp32(ctx)) {
     launch_band_build<float>(ctx->A, Bp, ctx->kl, ctx->ku, ctx->ne, ctx->dz, (cxf *)ctx->band, ctx->s);
     CKC(band_factor<float>(ctx->n, ctx->kl, ctx->ku, ctx->ne, (cxf *)ctx->band, ctx->d_err, ctx->s));
+    launch_band_diag_inv<float>(ctx->n, ctx->kl, ctx->ku, ctx->ne, (const cxf *)ctx->band, (cxf *)ctx->dinv, ctx->s);
   } else {
     launch_band_build<double>(ctx->A, Bp, ctx->kl, ctx->ku, ctx->ne, ctx->dz, (cxd *)ctx->band, ctx->s);
     CKC(band_factor<double>(ctx->n, ctx->kl, ctx->ku, ctx->ne, (cxd *)ctx->band, ctx->d_err, ctx->s));
@@ -232,7 +234,8 @@ void do_filter(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, cxd *Q, cxd *Qh, 
   const size_t xns = (size_t)n * m;
   if (!fp32(ctx)) {
     int k = ev_begin(ctx, ctx->ev_solve);
-    CKC(band_solve_sides<double, double>(n, ctx->kl, ctx->ku, ne, (const cxd *)ctx->band, BY, BhYh, 0, m, ctx->Xn,
+    CKC(band_solve_sides<double, double>(n, ctx->kl, ctx->ku, ne, (const cxd *)ctx->band, nullptr, BY, BhYh, 0, m,
+                                         ctx->Xn,
                                          cs ? nullptr : ctx->Xhn, xns, 0, (cxd *)ctx->ysc, nullptr, ctx->s));
     ev_end(ctx, ctx->ev_solve, k);
     launch_multishift_residual<double>(ctx->A, Bp, ne, ctx->dz, ctx->dw, ctx->Xn, BY, nullptr, Q, nullptr, m, nullptr,
@@ -244,7 +247,8 @@ void do_filter(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, cxd *Q, cxd *Qh, 
   } else {
     CKC(cudaMemsetAsync(ctx->d_done, 0, sizeof(int), ctx->s));
     int k0 = ev_begin(ctx, ctx->ev_solve);
-    CKC(band_solve_sides<float, double>(n, ctx->kl, ctx->ku, ne, (const cxf *)ctx->band, BY, BhYh, 0, m, ctx->Xn,
+    CKC(band_solve_sides<float, double>(n, ctx->kl, ctx->ku, ne, (const cxf *)ctx->band, (const cxf *)ctx->dinv, BY,
+                                        BhYh, 0, m, ctx->Xn,
                                         cs ? nullptr : ctx->Xhn, xns, 0, (cxf *)ctx->ysc, nullptr, ctx->s));
     ev_end(ctx, ctx->ev_solve, k0);
     int g = launch_colnorm2(BY, m, m, n, ctx->colp, ctx->s);
@@ -276,7 +280,8 @@ void do_filter(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, cxd *Q, cxd *Qh, 
       if (done) break;
       if (it + 1 < steps) {
         int ks = ev_begin(ctx, ctx->ev_solve);
-        CKC(band_solve_sides<float, float>(n, ctx->kl, ctx->ku, ne, (const cxf *)ctx->band, (const cxf *)ctx->Rn,
+        CKC(band_solve_sides<float, float>(n, ctx->kl, ctx->ku, ne, (const cxf *)ctx->band, (const cxf *)ctx->dinv,
+                                           (const cxf *)ctx->Rn,
                                            cs ? nullptr : (const cxf *)ctx->Rhn, xns, m, ctx->Xn,
                                            cs ? nullptr : ctx->Xhn, xns, 1, (cxf *)ctx->ysc, nullptr, ctx->s));
         ev_end(ctx, ctx->ev_solve, ks);
@@ -538,6 +543,7 @@ feast_nh_status feast_nh_init(feast_nh_ctx **out, const feast_nh_csr *A, const f
     ctx->band = dalloc<void>(ctx, (size_t)ne * n * (ctx->kl + ctx->ku + 1) * es);
     const size_t yse = f32 ? band_solve_scratch_elems<float>(n, m0, ne) : band_solve_scratch_elems<double>(n, m0, ne);
     ctx->ysc = dalloc<void>(ctx, yse * es);
+    if (f32) ctx->dinv = dalloc<void>(ctx, band_diag_inv_elems(n, ne) * sizeof(cxf));
     const size_t blk = (size_t)n * m0 * sizeof(cxd);
     ctx->Yw = dalloc<cxd>(ctx, blk);
     ctx->Yhw = dalloc<cxd>(ctx, blk);

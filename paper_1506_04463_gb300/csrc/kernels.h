@@ -18,10 +18,14 @@ cudaError_t band_factor(int n, int kl, int ku, int ne, cx<T> *band, int *d_err, 
 // stride m, element type Tin.  X (double complex, node stride xns) gets the
 // solution (mode 0) or has it added (mode 1).  Skipped when *skip != 0.
 template <typename T, typename Tin>
-cudaError_t band_solve_sides(int n, int kl, int ku, int ne, const cx<T> *band, const cx<Tin> *rhsR,
+cudaError_t band_solve_sides(int n, int kl, int ku, int ne, const cx<T> *band, const cx<T> *dinv, const cx<Tin> *rhsR,
                              const cx<Tin> *rhsL, size_t rns, int m, cxd *XR, cxd *XL, size_t xns, int mode,
                              cx<T> *ysc, const int *skip, cudaStream_t s);
 template <typename T> size_t band_solve_scratch_elems(int n, int m, int ne);
+// Inverses of the 16 x 16 diagonal blocks of L and U (FP32 solve path).
+template <typename T>
+void launch_band_diag_inv(int n, int kl, int ku, int ne, const cx<T> *band, cx<T> *dinv, cudaStream_t s);
+size_t band_diag_inv_elems(int n, int ne);
 template <typename T> bool band_fits(int kl, int ku);
 template <typename T> bool band_solve_fits(int kl, int ku);
 
