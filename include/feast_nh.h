@@ -89,7 +89,7 @@ typedef struct {
   double eps;         /* 1e-10  */
   double eta;         /* 1e-16  */
   double mu;          /* 0.1    */
-  double inner_tol;   /* 1e-10  */
+  double inner_tol;   /* 1e-11  */
   int32_t max_iter;   /* 100    */
   int32_t inner_max;  /* 12     */
   int32_t inner_kind; /* FEAST_NH_INNER_BANDED */
@@ -116,6 +116,9 @@ typedef struct {
    * triangular-solve kernel and of the multi-shift residual kernel */
   double t_solve_kernel_ms, t_resid_kernel_ms;
   int32_t n_solve_launches, n_resid_launches;
+  int32_t n_factorizations; /* shifted matrices factorised: ne, or ne/2 for a
+                               real pencil whose nodes come in conjugate pairs
+                               (Sec. 2.4, Table tab:solve)                    */
 } feast_nh_info;
 
 /* Fills *o with the defaults listed above. */

@@ -564,29 +564,38 @@ template <> struct SolveCfg<double> { static constexpr int NB = 16, R = 16, RPT 
 struct SolveSides {
   const void *rhs[2];
   cxd *X[2];
+  // node j uses factor slot fmap[j] & 0xffff; bit 16 set: the factors are
+  // the complex conjugates of that slot's (real pencil, conjugate node pair)
+  int fmap[kMaxNe];
 };
 
 template <typename T>
-__device__ __forceinline__ cx<T> lower_elem(const cx<T> *Bd, int W, int kl, int ku, bool herm, int r, int i) {
-  // strictly lower part of the forward factor: N -> L(r,i); H -> conj(U(i,r))
+__device__ __forceinline__ cx<T> cj_if(cx<T> v, bool c) {
+  if (c) v.im = -v.im;
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ cx<T> lower_elem(const cx<T> *Bd, int W, int kl, int ku, bool herm, bool cj, int r, int i) {
+  // strictly lower part of the forward factor: N -> L(r,i); H -> conj(U(i,r));
+  // cj: factors of the conjugate node
   int d = r - i;
   if (!herm) {
     if (d > kl) return mk<T>(0, 0);
-    return Bd[(size_t)r * W + (kl - d)];
+    return cj_if(Bd[(size_t)r * W + (kl - d)], cj);
   }
   if (d > ku) return mk<T>(0, 0);
-  return conj(Bd[(size_t)i * W + (kl + d)]);
+  return cj_if(Bd[(size_t)i * W + (kl + d)], !cj);
 }
 template <typename T>
-__device__ __forceinline__ cx<T> upper_elem(const cx<T> *Bd, int W, int kl, int ku, bool herm, int r, int i) {
+__device__ __forceinline__ cx<T> upper_elem(const cx<T> *Bd, int W, int kl, int ku, bool herm, bool cj, int r, int i) {
   // strictly upper part of the backward factor: N -> U(r,i); H -> conj(L(i,r))
   int d = i - r;
   if (!herm) {
     if (d > ku) return mk<T>(0, 0);
-    return Bd[(size_t)r * W + (kl + d)];
+    return cj_if(Bd[(size_t)r * W + (kl + d)], cj);
   }
   if (d > kl) return mk<T>(0, 0);
-  return conj(Bd[(size_t)i * W + (kl - d)]);
+  return cj_if(Bd[(size_t)i * W + (kl - d)], !cj);
 }
 
 template <typename T, typename Tin, int NB, int R, int RPT>
@@ -609,7 +618,8 @@ __global__ void __launch_bounds__(R *NB / RPT) k_band_solve(int n, int kl, int k
   const bool herm = side == 1;
   const int node = blockIdx.y;
   const int c0 = blockIdx.x * R;
-  const cx<T> *Bd = band + (size_t)node * bns;
+  const bool cj = (io.fmap[node] >> 16) & 1;
+  const cx<T> *Bd = band + (size_t)(io.fmap[node] & 0xffff) * bns;
   const cx<Tin> *Rh = reinterpret_cast<const cx<Tin> *>(io.rhs[side]) + (size_t)node * rns;
   cxd *Xn = io.X[side] + (size_t)node * xns;
   cx<T> *Ys = ysc + (((size_t)side * gridDim.y + node) * gridDim.x + blockIdx.x) * (size_t)n * R;
@@ -631,7 +641,7 @@ __global__ void __launch_bounds__(R *NB / RPT) k_band_solve(int n, int kl, int k
           int rr = idx / TWl, ii = idx - rr * TWl;
           int r = kb + rr, i = i0 + ii;
           cx<T> v = mk<T>(0, 0);
-          if (rr < nbk && i >= 0 && i < r) v = lower_elem(Bd, W, kl, ku, false, r, i);
+          if (rr < nbk && i >= 0 && i < r) v = lower_elem(Bd, W, kl, ku, false, cj, r, i);
           Ms[idx] = v;
         }
       } else {
@@ -639,11 +649,11 @@ __global__ void __launch_bounds__(R *NB / RPT) k_band_solve(int n, int kl, int k
           int ii = idx / NB, rr = idx - ii * NB;
           int r = kb + rr, i = i0 + ii;
           cx<T> v = mk<T>(0, 0);
-          if (rr < nbk && i >= 0 && i < r) v = lower_elem(Bd, W, kl, ku, true, r, i);
+          if (rr < nbk && i >= 0 && i < r) v = lower_elem(Bd, W, kl, ku, true, cj, r, i);
           Ms[rr * TWl + ii] = v;
         }
       }
-      if (tid < nbk) dg[tid] = herm ? conj(Bd[(size_t)(kb + tid) * W + kl]) : mk<T>(1, 0);
+      if (tid < nbk) dg[tid] = herm ? cj_if(Bd[(size_t)(kb + tid) * W + kl], !cj) : mk<T>(1, 0);
 #pragma unroll
       for (int s = 0; s < RPT; ++s) {
         int r = kb + rg + G * s;
@@ -692,7 +702,7 @@ __global__ void __launch_bounds__(R *NB / RPT) k_band_solve(int n, int kl, int k
           int rr = idx / TWu, ii = idx - rr * TWu;
           int r = kb + rr, i = kb + ii;
           cx<T> v = mk<T>(0, 0);
-          if (rr < nbk && i > r && i < n) v = upper_elem(Bd, W, kl, ku, false, r, i);
+          if (rr < nbk && i > r && i < n) v = upper_elem(Bd, W, kl, ku, false, cj, r, i);
           Ms[idx] = v;
         }
       } else {
@@ -700,11 +710,11 @@ __global__ void __launch_bounds__(R *NB / RPT) k_band_solve(int n, int kl, int k
           int ii = idx / NB, rr = idx - ii * NB;
           int r = kb + rr, i = kb + ii;
           cx<T> v = mk<T>(0, 0);
-          if (rr < nbk && i > r && i < n) v = upper_elem(Bd, W, kl, ku, true, r, i);
+          if (rr < nbk && i > r && i < n) v = upper_elem(Bd, W, kl, ku, true, cj, r, i);
           Ms[rr * TWu + ii] = v;
         }
       }
-      if (tid < nbk) dg[tid] = herm ? mk<T>(1, 0) : Bd[(size_t)(kb + tid) * W + kl];
+      if (tid < nbk) dg[tid] = herm ? mk<T>(1, 0) : cj_if(Bd[(size_t)(kb + tid) * W + kl], cj);
 #pragma unroll
       for (int s = 0; s < RPT; ++s) {
         int r = kb + rg + G * s;
@@ -881,7 +891,11 @@ __device__ __forceinline__ void ks_fetch(const cxf *Bd, const cxf *Dv, int n, in
 
 template <bool HERM, typename Tin>
 __device__ __forceinline__ void ks_body(int n, int kl, int ku, const cxf *Bd, const cxf *Dv, const cx<Tin> *Rh,
-                                        cxd *Xn, cxf *Ys, int m, int mode, int c0, unsigned char *smem_raw) {
+                                        cxd *Xn, cxf *Ys, int m, int mode, int c0, bool cj,
+                                        unsigned char *smem_raw) {
+  // conjugate the factor values read from the tiles: HERM (conjugate-transpose
+  // solve) and cj (conjugate node) toggle it
+  const float vsg = (HERM != cj) ? -1.f : 1.f;
   using namespace ks;
   const int W = kl + ku + 1;
   const int bwmax = max(kl, ku);
@@ -948,7 +962,7 @@ __device__ __forceinline__ void ks_body(int n, int kl, int ku, const cxf *Bd, co
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
           mv[q] = Ms[(rl + 8 * q) * TWP + col];
-          if (HERM) mv[q].im = -mv[q].im;
+          mv[q].im *= vsg;
         }
 #pragma unroll
         for (int t = 0; t < 4; ++t) yv[t] = ring[slot * R + cl + 4 * t];
@@ -979,12 +993,8 @@ __device__ __forceinline__ void ks_body(int n, int kl, int ku, const cxf *Bd, co
         a.re = __shfl_sync(full, acc2.re, (lane & 16) | p);
         a.im = __shfl_sync(full, acc2.im, (lane & 16) | p);
         cxf dv;
-        if (HERM) {
-          dv = dg[p * DLD + tr];
-          dv.im = -dv.im;
-        } else {
-          dv = dg[tr * DLD + p];
-        }
+        dv = HERM ? dg[p * DLD + tr] : dg[tr * DLD + p];
+        dv.im *= vsg;
         cfma(x, dv, a);
       }
       acc2 = x;
@@ -1014,15 +1024,17 @@ __global__ void __launch_bounds__(ks::NT) k_band_solve_ks(int n, int kl, int ku,
   const int side = blockIdx.z;
   const int node = blockIdx.y;
   const int c0 = blockIdx.x * ks::R;
-  const cxf *Bd = band + (size_t)node * bns;
+  const int slot = io.fmap[node] & 0xffff;
+  const bool cj = (io.fmap[node] >> 16) & 1;
+  const cxf *Bd = band + (size_t)slot * bns;
   const cx<Tin> *Rh = reinterpret_cast<const cx<Tin> *>(side ? io.rhs[1] : io.rhs[0]) + (size_t)node * rns;
   cxd *Xn = (side ? io.X[1] : io.X[0]) + (size_t)node * xns;
   cxf *Ys = ysc + (((size_t)side * gridDim.y + node) * gridDim.x + blockIdx.x) * (size_t)n * ks::R;
-  const cxf *Dv = dinv + (size_t)node * ceil_div(n, ks::NB) * (2 * ks::NB * ks::NB);
+  const cxf *Dv = dinv + (size_t)slot * ceil_div(n, ks::NB) * (2 * ks::NB * ks::NB);
   if (side)
-    ks_body<true, Tin>(n, kl, ku, Bd, Dv, Rh, Xn, Ys, m, mode, c0, smem_raw);
+    ks_body<true, Tin>(n, kl, ku, Bd, Dv, Rh, Xn, Ys, m, mode, c0, cj, smem_raw);
   else
-    ks_body<false, Tin>(n, kl, ku, Bd, Dv, Rh, Xn, Ys, m, mode, c0, smem_raw);
+    ks_body<false, Tin>(n, kl, ku, Bd, Dv, Rh, Xn, Ys, m, mode, c0, cj, smem_raw);
 }
 
 static size_t solve_smem_ks(int kl, int ku) {
@@ -1043,14 +1055,15 @@ static size_t solve_smem(int kl, int ku) {
 // rhs/X pointers for the two sides are packed by the caller through the
 // globals below (set by band_solve_sides).
 template <typename T, typename Tin>
-cudaError_t band_solve_sides(int n, int kl, int ku, int ne, const cx<T> *band, const cx<T> *dinv, const cx<Tin> *rhsR,
-                             const cx<Tin> *rhsL, size_t rns, int m, cxd *XR, cxd *XL, size_t xns, int mode,
-                             cx<T> *ysc, const int *skip, cudaStream_t s) {
+cudaError_t band_solve_sides(int n, int kl, int ku, int ne, const int *fmap, const cx<T> *band, const cx<T> *dinv,
+                             const cx<Tin> *rhsR, const cx<Tin> *rhsL, size_t rns, int m, cxd *XR, cxd *XL,
+                             size_t xns, int mode, cx<T> *ysc, const int *skip, cudaStream_t s) {
   SolveSides io;
   io.rhs[0] = rhsR;
   io.rhs[1] = rhsL ? rhsL : rhsR;
   io.X[0] = XR;
   io.X[1] = XL ? XL : XR;
+  for (int j = 0; j < kMaxNe; ++j) io.fmap[j] = (fmap && j < ne) ? fmap[j] : j;
   const int nsides = (rhsL && XL) ? 2 : 1;
   const size_t bns = (size_t)n * (kl + ku + 1);
   if constexpr (std::is_same<T, float>::value) {
@@ -1074,13 +1087,13 @@ cudaError_t band_solve_sides(int n, int kl, int ku, int ne, const cx<T> *band, c
   }
   return cudaGetLastError();
 }
-template cudaError_t band_solve_sides<float, float>(int, int, int, int, const cxf *, const cxf *, const cxf *, const cxf *,
+template cudaError_t band_solve_sides<float, float>(int, int, int, int, const int *, const cxf *, const cxf *, const cxf *, const cxf *,
                                                     size_t, int, cxd *, cxd *, size_t, int, cxf *, const int *,
                                                     cudaStream_t);
-template cudaError_t band_solve_sides<float, double>(int, int, int, int, const cxf *, const cxf *, const cxd *, const cxd *,
+template cudaError_t band_solve_sides<float, double>(int, int, int, int, const int *, const cxf *, const cxf *, const cxd *, const cxd *,
                                                      size_t, int, cxd *, cxd *, size_t, int, cxf *, const int *,
                                                      cudaStream_t);
-template cudaError_t band_solve_sides<double, double>(int, int, int, int, const cxd *, const cxd *, const cxd *, const cxd *,
+template cudaError_t band_solve_sides<double, double>(int, int, int, int, const int *, const cxd *, const cxd *, const cxd *, const cxd *,
                                                       size_t, int, cxd *, cxd *, size_t, int, cxd *, const int *,
                                                       cudaStream_t);
 

@@ -37,6 +37,9 @@ struct feast_nh_ctx {
   bool hasB = false;
   std::vector<void *> allocs;
   int kl = -1, ku = -1;
+  int nf = 0;              // shifted matrices factorised (ne, or ne/2 with conjugate node pairs)
+  std::vector<int> fmap;   // node -> factor slot | conjugate << 16
+  cxd *dzf = nullptr;      // shifts of the factorised matrices
   bool factored = false;
   void *band = nullptr;
   void *ysc = nullptr;
@@ -194,12 +197,12 @@ void factorize(feast_nh_ctx *ctx) {
   CKC(cudaEventRecord(ctx->ev[4], ctx->s));
   CKC(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->s));
   if (fp32(ctx)) {
-    launch_band_build<float>(ctx->A, Bp, ctx->kl, ctx->ku, ctx->ne, ctx->dz, (cxf *)ctx->band, ctx->s);
-    CKC(band_factor<float>(ctx->n, ctx->kl, ctx->ku, ctx->ne, (cxf *)ctx->band, ctx->d_err, ctx->s));
-    launch_band_diag_inv<float>(ctx->n, ctx->kl, ctx->ku, ctx->ne, (const cxf *)ctx->band, (cxf *)ctx->dinv, ctx->s);
+    launch_band_build<float>(ctx->A, Bp, ctx->kl, ctx->ku, ctx->nf, ctx->dzf, (cxf *)ctx->band, ctx->s);
+    CKC(band_factor<float>(ctx->n, ctx->kl, ctx->ku, ctx->nf, (cxf *)ctx->band, ctx->d_err, ctx->s));
+    launch_band_diag_inv<float>(ctx->n, ctx->kl, ctx->ku, ctx->nf, (const cxf *)ctx->band, (cxf *)ctx->dinv, ctx->s);
   } else {
-    launch_band_build<double>(ctx->A, Bp, ctx->kl, ctx->ku, ctx->ne, ctx->dz, (cxd *)ctx->band, ctx->s);
-    CKC(band_factor<double>(ctx->n, ctx->kl, ctx->ku, ctx->ne, (cxd *)ctx->band, ctx->d_err, ctx->s));
+    launch_band_build<double>(ctx->A, Bp, ctx->kl, ctx->ku, ctx->nf, ctx->dzf, (cxd *)ctx->band, ctx->s);
+    CKC(band_factor<double>(ctx->n, ctx->kl, ctx->ku, ctx->nf, (cxd *)ctx->band, ctx->d_err, ctx->s));
   }
   CKC(cudaEventRecord(ctx->ev[5], ctx->s));
   int herr = 0;
@@ -234,7 +237,8 @@ void do_filter(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, cxd *Q, cxd *Qh, 
   const size_t xns = (size_t)n * m;
   if (!fp32(ctx)) {
     int k = ev_begin(ctx, ctx->ev_solve);
-    CKC(band_solve_sides<double, double>(n, ctx->kl, ctx->ku, ne, (const cxd *)ctx->band, nullptr, BY, BhYh, 0, m,
+    CKC(band_solve_sides<double, double>(n, ctx->kl, ctx->ku, ne, ctx->fmap.data(), (const cxd *)ctx->band, nullptr,
+                                         BY, BhYh, 0, m,
                                          ctx->Xn,
                                          cs ? nullptr : ctx->Xhn, xns, 0, (cxd *)ctx->ysc, nullptr, ctx->s));
     ev_end(ctx, ctx->ev_solve, k);
@@ -247,7 +251,8 @@ void do_filter(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, cxd *Q, cxd *Qh, 
   } else {
     CKC(cudaMemsetAsync(ctx->d_done, 0, sizeof(int), ctx->s));
     int k0 = ev_begin(ctx, ctx->ev_solve);
-    CKC(band_solve_sides<float, double>(n, ctx->kl, ctx->ku, ne, (const cxf *)ctx->band, (const cxf *)ctx->dinv, BY,
+    CKC(band_solve_sides<float, double>(n, ctx->kl, ctx->ku, ne, ctx->fmap.data(), (const cxf *)ctx->band,
+                                        (const cxf *)ctx->dinv, BY,
                                         BhYh, 0, m, ctx->Xn,
                                         cs ? nullptr : ctx->Xhn, xns, 0, (cxf *)ctx->ysc, nullptr, ctx->s));
     ev_end(ctx, ctx->ev_solve, k0);
@@ -280,7 +285,8 @@ void do_filter(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, cxd *Q, cxd *Qh, 
       if (done) break;
       if (it + 1 < steps) {
         int ks = ev_begin(ctx, ctx->ev_solve);
-        CKC(band_solve_sides<float, float>(n, ctx->kl, ctx->ku, ne, (const cxf *)ctx->band, (const cxf *)ctx->dinv,
+        CKC(band_solve_sides<float, float>(n, ctx->kl, ctx->ku, ne, ctx->fmap.data(), (const cxf *)ctx->band,
+                                           (const cxf *)ctx->dinv,
                                            (const cxf *)ctx->Rn,
                                            cs ? nullptr : (const cxf *)ctx->Rhn, xns, m, ctx->Xn,
                                            cs ? nullptr : ctx->Xhn, xns, 1, (cxf *)ctx->ysc, nullptr, ctx->s));
@@ -405,7 +411,7 @@ void feast_nh_default_opts(feast_nh_opts *o) {
   o->eps = 1e-10;
   o->eta = 1e-16;
   o->mu = 0.1;
-  o->inner_tol = 1e-10;
+  o->inner_tol = 1e-11;
   o->max_iter = 100;
   o->inner_max = 12;
   o->inner_kind = FEAST_NH_INNER_BANDED;
@@ -531,6 +537,35 @@ feast_nh_status feast_nh_init(feast_nh_ctx **out, const feast_nh_csr *A, const f
     REQ(ext[2] == 0, "a column index of A or B is outside [0, n)");
     ctx->kl = ext[0];
     ctx->ku = ext[1];
+    // Real pencil and a node set closed under conjugation (Sec. 2.4, Table
+    // tab:solve): (conj(z) B - A) = conj(z B - A), so only one matrix of each
+    // conjugate pair is factorised and the other uses the conjugated factors.
+    {
+      const bool real_pencil = !ctx->A.cplx && (!ctx->hasB || !ctx->B.cplx);
+      ctx->fmap.assign(ne, -1);
+      std::vector<cxd> zf;
+      for (int j = 0; j < ne; ++j) {
+        if (ctx->fmap[j] >= 0) continue;
+        int partner = -1;
+        if (real_pencil) {
+          const double tol = 1e-13 * (1.0 + std::hypot(ctx->hz[j].re, ctx->hz[j].im));
+          for (int k = 0; k < ne; ++k)
+            if (k != j && ctx->fmap[k] < 0 &&
+                std::hypot(ctx->hz[k].re - ctx->hz[j].re, ctx->hz[k].im + ctx->hz[j].im) <= tol) {
+              partner = k;
+              break;
+            }
+        }
+        const int slot = (int)zf.size();
+        const int rep = (partner >= 0 && ctx->hz[j].im < 0) ? partner : j;
+        zf.push_back(ctx->hz[rep]);
+        ctx->fmap[rep] = slot;
+        if (partner >= 0) ctx->fmap[rep == j ? partner : j] = slot | (1 << 16);
+      }
+      ctx->nf = (int)zf.size();
+      ctx->dzf = dalloc<cxd>(ctx, ctx->nf * sizeof(cxd));
+      CKC(cudaMemcpyAsync(ctx->dzf, zf.data(), ctx->nf * sizeof(cxd), cudaMemcpyHostToDevice, ctx->s));
+    }
     const bool f32 = fp32(ctx);
     const bool fits = f32 ? (band_fits<float>(ctx->kl, ctx->ku) && band_solve_fits<float>(ctx->kl, ctx->ku))
                           : (band_fits<double>(ctx->kl, ctx->ku) && band_solve_fits<double>(ctx->kl, ctx->ku));
@@ -540,10 +575,10 @@ feast_nh_status feast_nh_init(feast_nh_ctx **out, const feast_nh_csr *A, const f
       REQ(false, msg);
     }
     const size_t es = f32 ? sizeof(cxf) : sizeof(cxd);
-    ctx->band = dalloc<void>(ctx, (size_t)ne * n * (ctx->kl + ctx->ku + 1) * es);
+    ctx->band = dalloc<void>(ctx, (size_t)ctx->nf * n * (ctx->kl + ctx->ku + 1) * es);
     const size_t yse = f32 ? band_solve_scratch_elems<float>(n, m0, ne) : band_solve_scratch_elems<double>(n, m0, ne);
     ctx->ysc = dalloc<void>(ctx, yse * es);
-    if (f32) ctx->dinv = dalloc<void>(ctx, band_diag_inv_elems(n, ne) * sizeof(cxf));
+    if (f32) ctx->dinv = dalloc<void>(ctx, band_diag_inv_elems(n, ctx->nf) * sizeof(cxf));
     const size_t blk = (size_t)n * m0 * sizeof(cxd);
     ctx->Yw = dalloc<cxd>(ctx, blk);
     ctx->Yhw = dalloc<cxd>(ctx, blk);
@@ -650,6 +685,7 @@ feast_nh_status feast_nh_rr(feast_nh_ctx *ctx, const void *Q, const void *Qh, in
       info->max_res = ctx->h_st->max_res;
       info->kl = ctx->kl;
       info->ku = ctx->ku;
+      info->n_factorizations = ctx->nf;
     }
     int herr = 0;
     std::memcpy(&herr, ctx->h_small + 1, sizeof(int));
@@ -750,6 +786,7 @@ feast_nh_status feast_nh_solve(feast_nh_ctx *ctx, const void *Y0, const void *Yh
       info->t_resid_kernel_ms = ctx->ev_resid.ms;
       info->n_solve_launches = ctx->ev_solve.launches;
       info->n_resid_launches = ctx->ev_resid.launches;
+      info->n_factorizations = ctx->nf;
     }
     if (!conv) {
       ctx->err = "no convergence within max_iter outer iterations";

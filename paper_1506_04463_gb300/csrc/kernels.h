@@ -17,10 +17,12 @@ cudaError_t band_factor(int n, int kl, int ku, int ne, cx<T> *band, int *d_err, 
 // node-major blocks (or one shared block when rns == 0) of n x m with row
 // stride m, element type Tin.  X (double complex, node stride xns) gets the
 // solution (mode 0) or has it added (mode 1).  Skipped when *skip != 0.
+// fmap (host, ne entries, NULL: identity): node j uses factor slot fmap[j] &
+// 0xffff, conjugated when bit 16 is set.
 template <typename T, typename Tin>
-cudaError_t band_solve_sides(int n, int kl, int ku, int ne, const cx<T> *band, const cx<T> *dinv, const cx<Tin> *rhsR,
-                             const cx<Tin> *rhsL, size_t rns, int m, cxd *XR, cxd *XL, size_t xns, int mode,
-                             cx<T> *ysc, const int *skip, cudaStream_t s);
+cudaError_t band_solve_sides(int n, int kl, int ku, int ne, const int *fmap, const cx<T> *band, const cx<T> *dinv,
+                             const cx<Tin> *rhsR, const cx<Tin> *rhsL, size_t rns, int m, cxd *XR, cxd *XL,
+                             size_t xns, int mode, cx<T> *ysc, const int *skip, cudaStream_t s);
 template <typename T> size_t band_solve_scratch_elems(int n, int m, int ne);
 // Inverses of the 16 x 16 diagonal blocks of L and U (FP32 solve path).
 template <typename T>

@@ -45,7 +45,7 @@ class Info(C.Structure):
                 ("ku", C.c_int32), ("max_res", C.c_double), ("inner_res", C.c_double),
                 ("t_factor_ms", C.c_double), ("t_filter_ms", C.c_double), ("t_rr_ms", C.c_double),
                 ("t_total_ms", C.c_double), ("t_solve_kernel_ms", C.c_double), ("t_resid_kernel_ms", C.c_double),
-                ("n_solve_launches", C.c_int32), ("n_resid_launches", C.c_int32)]
+                ("n_solve_launches", C.c_int32), ("n_resid_launches", C.c_int32), ("n_factorizations", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

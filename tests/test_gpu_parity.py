@@ -176,3 +176,34 @@ def test_determinism():
     a = ctx.solve(dev(wk.Y0), dev(wk.Yh0))
     b = ctx.solve(dev(wk.Y0), dev(wk.Yh0))
     assert torch.equal(a["lam"], b["lam"]) and torch.equal(a["X"], b["X"])
+
+
+def _table_solve():
+    import os
+    rows = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "table_solve_counts.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, f, s = line.split()
+            rows[k] = (float(f), float(s))
+    return rows
+
+
+def test_conjugate_pair_factorisation_count():
+    # Table tab:solve: real non-symmetric with C = C^* needs ne/2
+    # factorisations; complex general needs ne.  Results stay those of the oracle.
+    rows = _table_solve()
+    wk = wl.config2(N=30, m0=48, ne=16)
+    ctx = make_ctx(wk, precision=F.PREC_FP32_IR)
+    out = ctx.solve(dev(wk.Y0), dev(wk.Yh0))
+    assert out["info"]["n_factorizations"] == rows["real_nonsymmetric_conj_contour"][0] * 16
+    assert out["m"] == 30 and match_rel(host(out["lam"]), wk.exact, 1e-3) < 1e-9
+    invariants(wk, out)
+    # the same real pencil on a contour that is not symmetric about the real axis
+    con = wl.Contour(0, complex(wk.contour.center) + 0.3 * wk.contour.r * 1j, wk.contour.r, ne=8)
+    ctx2 = F.FeastNH(wk.A, None, con, wk.m0)
+    out2 = ctx2.solve(dev(wk.Y0), dev(wk.Yh0))
+    assert out2["info"]["n_factorizations"] == 8
+    wkc = banded_workload(n=300, kl=5, ku=3)
+    ctx3 = make_ctx(wkc)
+    out3 = ctx3.solve(dev(wkc.Y0), dev(wkc.Yh0))
+    assert out3["info"]["n_factorizations"] == rows["complex_general"][0] * wkc.contour.ne
