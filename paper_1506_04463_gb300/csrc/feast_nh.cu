@@ -218,8 +218,10 @@ void factorize(feast_nh_ctx *ctx) {
   ctx->factored = true;
 }
 
-// Step 1 of Fig. alg:three on n x m blocks.
-void do_filter(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, cxd *Q, cxd *Qh, int m) {
+// Step 1 of Fig. alg:three on n x m blocks.  inner_tol: refinement target
+// (negative: opts.inner_tol).
+void do_filter(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, cxd *Q, cxd *Qh, int m, double inner_tol = -1.0) {
+  if (inner_tol < 0) inner_tol = ctx->o.inner_tol;
   if (!ctx->factored) factorize(ctx);
   const bool cs = cs_mode(ctx);
   const int n = ctx->n, ne = ctx->ne;
@@ -274,8 +276,8 @@ void do_filter(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, cxd *Q, cxd *Qh, 
                                           ctx->part + (size_t)gm * ne * m, m, nullptr, ctx->s);
         ev_end(ctx, ctx->ev_resid, kr);
       }
-      launch_residual_check(ctx->part, gm, ne, m, ctx->bynorm2, cs ? 1 : 2, ctx->o.inner_tol, ctx->d_maxrel,
-                            ctx->d_done, ctx->s);
+      launch_residual_check(ctx->part, gm, ne, m, ctx->bynorm2, cs ? 1 : 2, inner_tol, ctx->d_maxrel, ctx->d_done,
+                            ctx->s);
       // one 4-byte read per refinement step decides whether to go on
       CKC(cudaMemcpyAsync(ctx->h_small + 2, ctx->d_done, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
       CKC(cudaStreamSynchronize(ctx->s));
@@ -726,7 +728,11 @@ feast_nh_status feast_nh_solve(feast_nh_ctx *ctx, const void *Y0, const void *Yh
     for (it = 1; it <= ctx->o.max_iter; ++it) {
       if (!ctx->factored) factorize(ctx);
       CKC(cudaEventRecord(ctx->ev[1], s));
-      do_filter(ctx, ctx->Yw, ctx->Yhw, ctx->Qw, ctx->Qhw, m);
+      // The first iteration only supplies the start subspace of the second,
+      // whose filter damps its errors by the convergence rate: its shifted
+      // systems are refined to 1e-4 only; later iterations to opts.inner_tol.
+      const double tol_it = it == 1 ? std::fmax(ctx->o.inner_tol, 1e-4) : ctx->o.inner_tol;
+      do_filter(ctx, ctx->Yw, ctx->Yhw, ctx->Qw, ctx->Qhw, m, tol_it);
       CKC(cudaEventRecord(ctx->ev[2], s));
       mt = do_rr(ctx, ctx->Qw, ctx->Qhw, m, ctx->Yw, ctx->Yhw);
       CKC(cudaEventRecord(ctx->ev[3], s));
