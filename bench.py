@@ -190,6 +190,10 @@ def run_ours(args, rank, world, local_rank):
     solve_flops = 2 * ne * m * (n * (kl + ku)) * 8.0
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12       # TFLOP/s at the max SM clock
     fp64_peak = 1.25                                          # nominal FP64 TFLOP/s of the part
+    # DRAM bytes of one k_band_solve_ks launch at this workload, from the ncu
+    # capture summarised in profiles/k_band_solve_ks_convdiff2d.md (refinement
+    # sweep; the kernel has not changed since)
+    solve_traffic = 13.47e9 + 4.39e9 if (prec == F.PREC_FP32_IR and args.N == 300) else None
     roof = None
     if n_solve:
         avg = solve_ms / n_solve
@@ -197,7 +201,7 @@ def run_ours(args, rank, world, local_rank):
         peak = fp32_peak if prec == F.PREC_FP32_IR else fp64_peak
         roof = {"kernel": "k_band_solve_ks" if prec == F.PREC_FP32_IR else "k_band_solve",
                 "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-                "frac": round(ach / peak, 4), "traffic": None, "avg_launch_ms": round(avg, 3),
+                "frac": round(ach / peak, 4), "traffic": solve_traffic, "avg_launch_ms": round(avg, 3),
                 "launches": n_solve, "flops_per_launch": solve_flops,
                 "peak_note": ("FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock" if prec == F.PREC_FP32_IR
                               else "FP64 nominal 1.25 TFLOP/s")}
