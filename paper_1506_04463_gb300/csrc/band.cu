@@ -864,20 +864,28 @@ __device__ __forceinline__ void ks_fetch(const cxf *Bd, const cxf *Dv, int n, in
   const int bw = fwd ? (HERM ? ku : kl) : (HERM ? kl : ku);
   const int TWl = bw + NB;
   const int ibase = fwd ? kb - bw : kb;
-  for (int idx = threadIdx.x; idx < NB * TWl; idx += NT) {
-    int rr, ii;
-    if (!HERM) {
-      rr = idx / TWl;
-      ii = idx - rr * TWl;
-    } else {
-      ii = idx / NB;
-      rr = idx - ii * NB;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (!HERM) {
+    // warp = tile row, lanes along the row (consecutive band entries)
+    for (int rr = warp; rr < NB; rr += NT / 32) {
+      const int r = kb + rr;
+      cxf *dst = Mb + rr * TWP;
+      const cxf *srow = Bd + (size_t)r * W + (kl - r);  // srow[i] = band(r, i)
+      for (int ii = lane; ii < TWl; ii += 32) {
+        const int i = ibase + ii;
+        const bool ok = rr < nbk && (fwd ? (i >= 0 && i < r && r - i <= bw) : (i > r && i < n && i - r <= bw));
+        cp_async8(dst + ii, ok ? srow + i : Bd, ok);
+      }
     }
-    const int r = kb + rr, i = ibase + ii;
-    bool ok = rr < nbk && (fwd ? (i >= 0 && i < r && r - i <= bw) : (i > r && i < n && i - r <= bw));
-    const cxf *src = Bd;
-    if (ok) src = HERM ? Bd + (size_t)i * W + (r - i + kl) : Bd + (size_t)r * W + (i - r + kl);
-    cp_async8(Mb + rr * TWP + ii, src, ok);
+  } else {
+    // half-warp = tile column (one band row i), lanes along the 16 tile rows
+    const int rr = lane & 15;
+    const int r = kb + rr;
+    for (int ii = 2 * warp + (lane >> 4); ii < TWl; ii += NT / 16) {
+      const int i = ibase + ii;
+      const bool ok = rr < nbk && (fwd ? (i >= 0 && i < r && r - i <= bw) : (i > r && i < n && i - r <= bw));
+      cp_async8(Mb + rr * TWP + ii, ok ? Bd + (size_t)i * W + (r - i + kl) : Bd, ok);
+    }
   }
   // inverse of the diagonal block: L11^{-1} for N-forward / H-backward,
   // U11^{-1} for N-backward / H-forward (the H sides use its conjugate transpose)
