@@ -199,7 +199,7 @@ def run_ours(args, rank, world, local_rank):
         avg = solve_ms / n_solve
         ach = solve_flops / (avg / 1e3) / 1e12
         peak = fp32_peak if prec == F.PREC_FP32_IR else fp64_peak
-        roof = {"kernel": "k_band_solve_ks" if prec == F.PREC_FP32_IR else "k_band_solve",
+        roof = {"kernel": "k_band_solve_tma" if prec == F.PREC_FP32_IR else "k_band_solve",
                 "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
                 "frac": round(ach / peak, 4), "traffic": solve_traffic, "avg_launch_ms": round(avg, 3),
                 "launches": n_solve, "flops_per_launch": solve_flops,

@@ -12,6 +12,7 @@
 // Storage (per node, row-major band): row r, offset t in [0, W), W = kl+ku+1,
 // holds entry (r, r-kl+t); after factorisation t < kl holds L (unit lower) and
 // t >= kl holds U.
+#include <cuda.h>
 #include <cooperative_groups.h>
 #include <type_traits>
 #include "kernels.h"
@@ -760,7 +761,8 @@ __global__ void __launch_bounds__(R *NB / RPT) k_band_solve(int n, int kl, int k
 // every node's factors, so that the triangular solves finish each 16-row
 // block with a dense product instead of a sequential substitution.  One warp
 // per block: lanes 0..15 form column j of L11^{-1}, lanes 16..31 column j of
-// U11^{-1}.  Output per (node, block): [L^{-1} | U^{-1}], each row-major.
+// U11^{-1}.  Output per (node, block): [L^{-1} | L^{-T} | U^{-1} | U^{-T}],
+// so that every solve reads its inverse with consecutive lanes.
 constexpr int DIB = 16;
 template <typename T>
 __device__ __forceinline__ cx<T> band_ld(const cx<T> *B, size_t o) { return B[o]; }
@@ -808,9 +810,13 @@ __global__ void __launch_bounds__(256) k_band_diag_inv(int n, int kl, int ku, co
       x[i] = cdiv(v, Ub[warp][i][i]);
     }
   }
-  cx<T> *out = dinv + ((size_t)node * nblk + b) * (2 * DIB * DIB) + (lane < 16 ? 0 : DIB * DIB);
+  // [L^{-1} | L^{-T} | U^{-1} | U^{-T}], each row-major 16 x 16
+  cx<T> *out = dinv + ((size_t)node * nblk + b) * (4 * DIB * DIB) + (lane < 16 ? 0 : 2 * DIB * DIB);
 #pragma unroll
-  for (int i = 0; i < DIB; ++i) out[i * DIB + j] = x[i];
+  for (int i = 0; i < DIB; ++i) {
+    out[i * DIB + j] = x[i];
+    out[DIB * DIB + j * DIB + i] = x[i];
+  }
 }
 
 template <typename T>
@@ -820,7 +826,30 @@ void launch_band_diag_inv(int n, int kl, int ku, int ne, const cx<T> *band, cx<T
   note_launch();
 }
 template void launch_band_diag_inv<float>(int, int, int, int, const cxf *, cxf *, cudaStream_t);
-size_t band_diag_inv_elems(int n, int ne) { return (size_t)ne * ceil_div(n, DIB) * 2 * DIB * DIB; }
+size_t band_diag_inv_elems(int n, int ne) { return (size_t)ne * ceil_div(n, DIB) * 4 * DIB * DIB; }
+
+// Transposed copy of the factors for the conjugate-transpose solves: row r of
+// Bt holds column r of the factored band (lower width ku, upper width kl), so
+// that both sides read their tiles along rows.
+__global__ void k_band_transpose(int n, int kl, int ku, int nslots, const cxf *__restrict__ B, cxf *__restrict__ Bt) {
+  const int W = kl + ku + 1;
+  const size_t per = (size_t)n * W, total = per * nslots;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t slot = e / per, rem = e - slot * per;
+    const int r = (int)(rem / W), tp = (int)(rem - (size_t)r * W);
+    const int i = r - ku + tp;  // Bt(r, tp) = B entry (i, r)
+    cxf v = mk(0.f, 0.f);
+    if (i >= 0 && i < n) v = B[slot * per + (size_t)i * W + (kl + ku - tp)];
+    Bt[e] = v;
+  }
+}
+void launch_band_transpose(int n, int kl, int ku, int nslots, const cxf *B, cxf *Bt, cudaStream_t s) {
+  const size_t total = (size_t)n * (kl + ku + 1) * nslots;
+  size_t g = (total + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  k_band_transpose<<<(unsigned)g, 256, 0, s>>>(n, kl, ku, nslots, B, Bt);
+  note_launch();
+}
 
 // FP32 variant.  The band range of each row block is split across the 8 warps
 // of the CTA; each lane keeps a 2 x 4 register tile (rows rl+8q, columns
@@ -891,7 +920,7 @@ __device__ __forceinline__ void ks_fetch(const cxf *Bd, const cxf *Dv, int n, in
   // U11^{-1} for N-backward / H-forward (the H sides use its conjugate transpose)
   {
     const bool useL = fwd != HERM;
-    const cxf *src = Dv + (size_t)b * (2 * NB * NB) + (useL ? 0 : NB * NB);
+    const cxf *src = Dv + (size_t)b * (4 * NB * NB) + (useL ? 0 : 2 * NB * NB);
     for (int e = threadIdx.x; e < NB * NB; e += NT) cp_async8(db + (e / NB) * DLD + e % NB, src + e, true);
   }
   cp_async_commit();
@@ -1038,7 +1067,7 @@ __global__ void __launch_bounds__(ks::NT) k_band_solve_ks(int n, int kl, int ku,
   const cx<Tin> *Rh = reinterpret_cast<const cx<Tin> *>(side ? io.rhs[1] : io.rhs[0]) + (size_t)node * rns;
   cxd *Xn = (side ? io.X[1] : io.X[0]) + (size_t)node * xns;
   cxf *Ys = ysc + (((size_t)side * gridDim.y + node) * gridDim.x + blockIdx.x) * (size_t)n * ks::R;
-  const cxf *Dv = dinv + (size_t)slot * ceil_div(n, ks::NB) * (2 * ks::NB * ks::NB);
+  const cxf *Dv = dinv + (size_t)slot * ceil_div(n, ks::NB) * (4 * ks::NB * ks::NB);
   if (side)
     ks_body<true, Tin>(n, kl, ku, Bd, Dv, Rh, Xn, Ys, m, mode, c0, cj, smem_raw);
   else
@@ -1050,6 +1079,292 @@ static size_t solve_smem_ks(int kl, int ku) {
   return ((size_t)2 * ks::NB * ks::tw_pad(bwmax) + (size_t)ks::ring_rows(bwmax) * ks::R +
           (size_t)ks::WARPS * ks::NB * ks::RED_LD + 2 * ks::NB * ks::DLD) * sizeof(cxf);
 }
+
+// ---------------------------------------------------------------------------
+// FP32 triangular solves with TMA tile loads.  Same block algorithm as above;
+// the factor tile of the next 16-row block (two boxes of BX band entries x 16
+// rows, from the row-major band for the right side and from its transpose for
+// the conjugate-transpose side) and the inverse of its diagonal block are
+// fetched by one thread with cp.async.bulk(.tensor) into the other buffer,
+// completing on an mbarrier; every thread waits on it with a bounded spin.
+// Row stride BX with BX/2 odd keeps the 8 rows read by a warp on distinct
+// shared-memory banks.
+// ---------------------------------------------------------------------------
+struct SolveTma {
+  CUtensorMap tmB, tmBt;  // 3D {W, n, slots} maps of the band and its transpose
+  int BX;                 // box width (entries), even, BX/2 odd
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *m, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(m)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *m, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *m, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(m)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *tm, int x, int y, int z, uint64_t *m) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(m))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *m) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(m))
+               : "memory");
+}
+
+namespace kt {
+constexpr int NB = 16, R = 16, WARPS = 16, NT = 32 * WARPS, RED_LD = R + 1;
+constexpr long long kSpinLimit = 1ll << 26;
+__host__ __device__ inline int ring_rows(int bw) { return ceil_div(bw + NB, NB) * NB; }
+__host__ __device__ inline size_t smem_bytes(int BX, int bwmax) {
+  return (size_t)(2 * 2 * NB * BX + 2 * 256 + ring_rows(bwmax) * R + WARPS * NB * RED_LD) * sizeof(cxf) +
+         2 * sizeof(uint64_t);
+}
+}  // namespace kt
+
+template <bool HERM, typename Tin>
+__device__ __forceinline__ void kt_body(int n, int klp, int kup, int BX, const CUtensorMap *tm, const cxf *Dv,
+                                        const cx<Tin> *Rh, cxd *Xn, cxf *Ys, int m, int mode, int c0, int slot,
+                                        bool cj, int *err, unsigned char *smem_raw) {
+  using namespace kt;
+  const float vsg = (HERM != cj) ? -1.f : 1.f;
+  const int lw = HERM ? kup : klp;  // lower width of the band the tiles come from
+  const int uw = HERM ? klp : kup;  // upper width
+  const int bwmax = max(lw, uw);
+  const int RB = ring_rows(bwmax);
+  const int BOXE = NB * BX;
+  cxf *Mbuf = reinterpret_cast<cxf *>(smem_raw);                  // 2 buffers x 2 boxes x BOXE
+  cxf *dbuf = Mbuf + (size_t)4 * BOXE;                              // 2 x 256, p-major inverse
+  cxf *ring = dbuf + 512;                                           // RB x R
+  cxf *red = ring + (size_t)RB * R;                                 // WARPS x NB x RED_LD
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(red + (size_t)WARPS * NB * RED_LD);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int rl = lane >> 2, cl = lane & 3;
+  const bool owner = warp < R / 2;
+  const int tc = 2 * (warp % (R / 2)) + (lane >> 4), tr = lane & 15;
+  const int gc = c0 + tc;
+  const bool cok = owner && gc < m;
+  const int nblk = ceil_div(n, NB);
+  const int nsteps = 2 * nblk;
+  const unsigned full = 0xffffffffu;
+  const uint32_t tx_bytes = (uint32_t)(2 * BOXE * sizeof(cxf) + 256 * sizeof(cxf));
+
+  auto issue = [&](int step) {
+    const bool f = step < nblk;
+    const int b = f ? step : 2 * nblk - 1 - step;
+    const int buf = step & 1;
+    cxf *dst = Mbuf + (size_t)buf * 2 * BOXE;
+    uint64_t *mb = &mbar[buf];
+    // TMA box origins must be even (16-byte aligned); the forward tile starts 16
+    // entries left of the band so that out-of-band entries come in as zeros
+    const int x0 = f ? -NB : (lw & ~1);
+    // inverse layouts per block: [L^{-1} | L^{-T} | U^{-1} | U^{-T}]; p-major reads
+    const int off = HERM ? (f ? 512 : 0) : (f ? 256 : 768);
+    mbar_expect_tx(mb, tx_bytes);
+    tma_load_3d(dst, tm, x0, b * NB, slot, mb);
+    tma_load_3d(dst + BOXE, tm, x0 + BX, b * NB, slot, mb);
+    bulk_load(dbuf + buf * 256, Dv + (size_t)b * 1024 + off, 256 * sizeof(cxf), mb);
+  };
+
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) issue(0);
+  bool timed_out = false;
+  for (int step = 0; step < nsteps; ++step) {
+    const bool fwd = step < nblk;
+    const int b = fwd ? step : 2 * nblk - 1 - step;
+    const int kb = b * NB;
+    const int nbk = min(NB, n - kb);
+    const int buf = step & 1;
+    const cxf *Ms = Mbuf + (size_t)buf * 2 * BOXE;
+    const cxf *dg = dbuf + buf * 256;
+    cxf acc2 = mk(0.f, 0.f);
+    {
+      const int r = kb + tr;
+      if (r < n && cok) acc2 = fwd ? ccast<float>(Rh[(size_t)r * m + gc]) : Ys[(size_t)r * R + tc];
+    }
+    if (!timed_out) {
+      long long spins = 0;
+      while (!mbar_try_wait(&mbar[buf], (uint32_t)((step >> 1) & 1))) {
+        if (++spins > kSpinLimit) {
+          timed_out = true;
+          atomicOr(err, DEVERR_TIMEOUT);
+          break;
+        }
+        if (spins > 32) __nanosleep(64);
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && step + 1 < nsteps && !timed_out) {
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      issue(step + 1);
+    }
+    // ---- GEMM over the rows already solved, split over warps ----
+    const int bw = fwd ? lw : uw;
+    int hlo, hhi;
+    if (fwd) {
+      hlo = max(0, kb - bw);
+      hhi = kb;
+    } else {
+      hlo = kb + nbk;
+      hhi = min(n, kb + nbk + bw);
+    }
+    const int len = max(hhi - hlo, 0);
+    const int per = ceil_div(len, WARPS);
+    const int wlo = hlo + warp * per, whi = min(hhi, wlo + per);
+    cxf acc[2][4];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) acc[q][t] = mk(0.f, 0.f);
+    if (wlo < whi) {
+      int rslot = wlo % RB;
+      // band offset of (row kb+rl+8q, column i) relative to the box origin:
+      // forward tt = i - r + lw + NB (origin -NB), backward tt = i - r + (lw & 1)
+      // (origin lw rounded down to even); always inside [0, 2 BX)
+      const int tbase = fwd ? lw + NB - kb : (lw & 1) - kb;
+#pragma unroll 4
+      for (int i = wlo; i < whi; ++i) {
+        cxf mv[2], yv[4];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int row = rl + 8 * q;
+          const int tt = i + tbase - row;
+          cxf v = Ms[row * BX + tt + (tt < BX ? 0 : BOXE - BX)];
+          v.im *= vsg;
+          mv[q] = v;
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) yv[t] = ring[rslot * R + cl + 4 * t];
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+          for (int t = 0; t < 4; ++t) cfma(acc[q][t], mv[q], yv[t]);
+        if (++rslot == RB) rslot = 0;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) red[(warp * NB + rl + 8 * q) * RED_LD + cl + 4 * t] = acc[q][t];
+    __syncthreads();
+    if (owner) {
+      cxf sum = mk(0.f, 0.f);
+#pragma unroll
+      for (int w = 0; w < WARPS; ++w) sum = sum + red[(w * NB + tr) * RED_LD + tc];
+      acc2 = acc2 - sum;
+      // in-block solve: x = D acc, D the inverse of the diagonal block (p-major)
+      cxf x = mk(0.f, 0.f);
+#pragma unroll
+      for (int p = 0; p < NB; ++p) {
+        cxf a;
+        a.re = __shfl_sync(full, acc2.re, (lane & 16) | p);
+        a.im = __shfl_sync(full, acc2.im, (lane & 16) | p);
+        cxf dv = dg[p * NB + tr];
+        dv.im *= vsg;
+        cfma(x, dv, a);
+      }
+      acc2 = x;
+      if (tr < nbk) {
+        const int r = kb + tr;
+        ring[(r % RB) * R + tc] = acc2;
+        if (fwd) {
+          Ys[(size_t)r * R + tc] = acc2;
+        } else if (cok) {
+          cxd *xp = Xn + (size_t)r * m + gc;
+          const cxd vd = ccast<double>(acc2);
+          *xp = mode ? (*xp + vd) : vd;
+        }
+      }
+    }
+  }
+}
+
+template <typename Tin>
+__global__ void __launch_bounds__(kt::NT) k_band_solve_tma(int n, int klp, int kup, const __grid_constant__ SolveTma tma,
+                                                           const cxf *dinv, SolveSides io, size_t rns, int m,
+                                                           size_t xns, int mode, cxf *ysc, int *err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int side = blockIdx.z;
+  const int node = blockIdx.y;
+  const int c0 = blockIdx.x * kt::R;
+  const int slot = io.fmap[node] & 0xffff;
+  const bool cj = (io.fmap[node] >> 16) & 1;
+  const cx<Tin> *Rh = reinterpret_cast<const cx<Tin> *>(side ? io.rhs[1] : io.rhs[0]) + (size_t)node * rns;
+  cxd *Xn = (side ? io.X[1] : io.X[0]) + (size_t)node * xns;
+  cxf *Ys = ysc + (((size_t)side * gridDim.y + node) * gridDim.x + blockIdx.x) * (size_t)n * kt::R;
+  const cxf *Dv = dinv + (size_t)slot * ceil_div(n, kt::NB) * 1024;
+  if (side)
+    kt_body<true, Tin>(n, klp, kup, tma.BX, &tma.tmBt, Dv, Rh, Xn, Ys, m, mode, c0, slot, cj, err, smem_raw);
+  else
+    kt_body<false, Tin>(n, klp, kup, tma.BX, &tma.tmB, Dv, Rh, Xn, Ys, m, mode, c0, slot, cj, err, smem_raw);
+}
+
+// Tensor maps of a band array (slots x n x W, 8-byte entries) for TMA loads of
+// 16-row boxes; BX as above.  Returns false if the band is too wide.
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static PFN_encodeTiled get_encode() {
+  static PFN_encodeTiled fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_encodeTiled>(p);
+  }
+  return fn;
+}
+int band_tma_box(int klp, int kup) {
+  // two boxes must cover: forward tiles [0, lw + 16), backward tiles up to
+  // uw + 16 + (lw & 1), for (lw, uw) = (klp, kup) and (kup, klp)
+  const int need = ceil_div(max(max(klp, kup) + 16, max(kup + 17 + (klp & 1), klp + 17 + (kup & 1))), 2);
+  int bx = need < 2 ? 2 : need;
+  while (bx % 4 != 2) ++bx;  // even, bx/2 odd
+  return bx;
+}
+bool band_tma_fits(int klp, int kup) {
+  const int bx = band_tma_box(klp, kup);
+  return bx <= 254 && kt::smem_bytes(bx, max(klp, kup)) <= 220 * 1024;
+}
+bool band_tma_make(void *tma_out, int n, int klp, int kup, int nslots, const cxf *band, const cxf *bandT) {
+  SolveTma *t = reinterpret_cast<SolveTma *>(tma_out);
+  PFN_encodeTiled enc = get_encode();
+  if (!enc || !band_tma_fits(klp, kup) || n < 16 || ((klp + kup + 1) & 1) || (klp & 1)) return false;
+  t->BX = band_tma_box(klp, kup);
+  const cuuint64_t W = (cuuint64_t)(klp + kup + 1);
+  const cuuint64_t dims[3] = {W, (cuuint64_t)n, (cuuint64_t)nslots};
+  const cuuint64_t strides[2] = {W * 8, W * 8 * (cuuint64_t)n};
+  const cuuint32_t box[3] = {(cuuint32_t)t->BX, 16, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  for (int k = 0; k < 2; ++k) {
+    CUresult r = enc(k == 0 ? &t->tmB : &t->tmBt, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+                     const_cast<cxf *>(k == 0 ? band : bandT), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+  }
+  return true;
+}
+size_t band_tma_bytes() { return sizeof(SolveTma); }
 
 template <typename T>
 static size_t solve_smem(int kl, int ku) {
@@ -1065,7 +1380,8 @@ static size_t solve_smem(int kl, int ku) {
 template <typename T, typename Tin>
 cudaError_t band_solve_sides(int n, int kl, int ku, int ne, const int *fmap, const cx<T> *band, const cx<T> *dinv,
                              const cx<Tin> *rhsR, const cx<Tin> *rhsL, size_t rns, int m, cxd *XR, cxd *XL,
-                             size_t xns, int mode, cx<T> *ysc, const int *skip, cudaStream_t s) {
+                             size_t xns, int mode, cx<T> *ysc, const int *skip, cudaStream_t s, const void *tma,
+                             int *err) {
   SolveSides io;
   io.rhs[0] = rhsR;
   io.rhs[1] = rhsL ? rhsL : rhsR;
@@ -1075,6 +1391,17 @@ cudaError_t band_solve_sides(int n, int kl, int ku, int ne, const int *fmap, con
   const int nsides = (rhsL && XL) ? 2 : 1;
   const size_t bns = (size_t)n * (kl + ku + 1);
   if constexpr (std::is_same<T, float>::value) {
+    if (tma) {
+      const SolveTma &tm = *reinterpret_cast<const SolveTma *>(tma);
+      const size_t smem = kt::smem_bytes(tm.BX, kl > ku ? kl : ku);
+      auto kern = k_band_solve_tma<Tin>;
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      dim3 grid(ceil_div(m, kt::R), ne, nsides);
+      kern<<<grid, kt::NT, smem, s>>>(n, kl, ku, tm, dinv, io, rns, m, xns, mode, ysc, err);
+      note_launch();
+      return cudaGetLastError();
+    }
     const size_t smem = solve_smem_ks(kl, ku);
     auto kern = k_band_solve_ks<Tin>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1097,13 +1424,13 @@ cudaError_t band_solve_sides(int n, int kl, int ku, int ne, const int *fmap, con
 }
 template cudaError_t band_solve_sides<float, float>(int, int, int, int, const int *, const cxf *, const cxf *, const cxf *, const cxf *,
                                                     size_t, int, cxd *, cxd *, size_t, int, cxf *, const int *,
-                                                    cudaStream_t);
+                                                    cudaStream_t, const void *, int *);
 template cudaError_t band_solve_sides<float, double>(int, int, int, int, const int *, const cxf *, const cxf *, const cxd *, const cxd *,
                                                      size_t, int, cxd *, cxd *, size_t, int, cxf *, const int *,
-                                                     cudaStream_t);
+                                                     cudaStream_t, const void *, int *);
 template cudaError_t band_solve_sides<double, double>(int, int, int, int, const int *, const cxd *, const cxd *, const cxd *, const cxd *,
                                                       size_t, int, cxd *, cxd *, size_t, int, cxd *, const int *,
-                                                      cudaStream_t);
+                                                      cudaStream_t, const void *, int *);
 
 template <typename T> size_t band_solve_scratch_elems(int n, int m, int ne) {
   constexpr int R = SolveCfg<T>::R;

@@ -89,7 +89,8 @@ __device__ __forceinline__ cxd csr_val(const CsrView &M, int64_t k) {
 }
 
 // Device error word bits.
-enum : int { DEVERR_ZERO_PIVOT = 1, DEVERR_QR_NOCONV = 2, DEVERR_SINGULAR_SMALL = 4, DEVERR_BAD_INDEX = 8 };
+enum : int { DEVERR_ZERO_PIVOT = 1, DEVERR_QR_NOCONV = 2, DEVERR_SINGULAR_SMALL = 4, DEVERR_BAD_INDEX = 8,
+             DEVERR_TIMEOUT = 16 };
 
 constexpr int kMaxNe = 64;     // quadrature nodes
 constexpr int kMaxM0 = 128;    // subspace size

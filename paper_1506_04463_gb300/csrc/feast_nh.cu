@@ -36,7 +36,10 @@ struct feast_nh_ctx {
   CsrView A{}, AH{}, B{}, BH{};
   bool hasB = false;
   std::vector<void *> allocs;
-  int kl = -1, ku = -1;
+  int kl = -1, ku = -1;     // band of (z B - A)
+  int klp = 0, kup = 0;     // stored band widths (kl rounded up to even, kl+ku+1 even)
+  void *bandT = nullptr;    // FP32: transposed factors for the conjugate-transpose solves
+  std::vector<unsigned char> tma;  // tensor maps of band and bandT (empty: no TMA path)
   int nf = 0;              // shifted matrices factorised (ne, or ne/2 with conjugate node pairs)
   std::vector<int> fmap;   // node -> factor slot | conjugate << 16
   cxd *dzf = nullptr;      // shifts of the factorised matrices
@@ -189,6 +192,8 @@ void ev_harvest(EvPool &p) {
   p.used = 0;
 }
 
+const void *tma_ptr(const feast_nh_ctx *ctx) { return ctx->tma.empty() ? nullptr : ctx->tma.data(); }
+
 bool cs_mode(const feast_nh_ctx *ctx) { return ctx->o.problem == FEAST_NH_PROBLEM_COMPLEX_SYMMETRIC; }
 bool fp32(const feast_nh_ctx *ctx) { return ctx->o.precision == FEAST_NH_PREC_FP32_IR; }
 
@@ -197,12 +202,14 @@ void factorize(feast_nh_ctx *ctx) {
   CKC(cudaEventRecord(ctx->ev[4], ctx->s));
   CKC(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->s));
   if (fp32(ctx)) {
-    launch_band_build<float>(ctx->A, Bp, ctx->kl, ctx->ku, ctx->nf, ctx->dzf, (cxf *)ctx->band, ctx->s);
-    CKC(band_factor<float>(ctx->n, ctx->kl, ctx->ku, ctx->nf, (cxf *)ctx->band, ctx->d_err, ctx->s));
-    launch_band_diag_inv<float>(ctx->n, ctx->kl, ctx->ku, ctx->nf, (const cxf *)ctx->band, (cxf *)ctx->dinv, ctx->s);
+    launch_band_build<float>(ctx->A, Bp, ctx->klp, ctx->kup, ctx->nf, ctx->dzf, (cxf *)ctx->band, ctx->s);
+    CKC(band_factor<float>(ctx->n, ctx->klp, ctx->kup, ctx->nf, (cxf *)ctx->band, ctx->d_err, ctx->s));
+    launch_band_diag_inv<float>(ctx->n, ctx->klp, ctx->kup, ctx->nf, (const cxf *)ctx->band, (cxf *)ctx->dinv, ctx->s);
+    if (!ctx->tma.empty())
+      launch_band_transpose(ctx->n, ctx->klp, ctx->kup, ctx->nf, (const cxf *)ctx->band, (cxf *)ctx->bandT, ctx->s);
   } else {
-    launch_band_build<double>(ctx->A, Bp, ctx->kl, ctx->ku, ctx->nf, ctx->dzf, (cxd *)ctx->band, ctx->s);
-    CKC(band_factor<double>(ctx->n, ctx->kl, ctx->ku, ctx->nf, (cxd *)ctx->band, ctx->d_err, ctx->s));
+    launch_band_build<double>(ctx->A, Bp, ctx->klp, ctx->kup, ctx->nf, ctx->dzf, (cxd *)ctx->band, ctx->s);
+    CKC(band_factor<double>(ctx->n, ctx->klp, ctx->kup, ctx->nf, (cxd *)ctx->band, ctx->d_err, ctx->s));
   }
   CKC(cudaEventRecord(ctx->ev[5], ctx->s));
   int herr = 0;
@@ -239,7 +246,7 @@ void do_filter(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, cxd *Q, cxd *Qh, 
   const size_t xns = (size_t)n * m;
   if (!fp32(ctx)) {
     int k = ev_begin(ctx, ctx->ev_solve);
-    CKC(band_solve_sides<double, double>(n, ctx->kl, ctx->ku, ne, ctx->fmap.data(), (const cxd *)ctx->band, nullptr,
+    CKC(band_solve_sides<double, double>(n, ctx->klp, ctx->kup, ne, ctx->fmap.data(), (const cxd *)ctx->band, nullptr,
                                          BY, BhYh, 0, m,
                                          ctx->Xn,
                                          cs ? nullptr : ctx->Xhn, xns, 0, (cxd *)ctx->ysc, nullptr, ctx->s));
@@ -253,10 +260,9 @@ void do_filter(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, cxd *Q, cxd *Qh, 
   } else {
     CKC(cudaMemsetAsync(ctx->d_done, 0, sizeof(int), ctx->s));
     int k0 = ev_begin(ctx, ctx->ev_solve);
-    CKC(band_solve_sides<float, double>(n, ctx->kl, ctx->ku, ne, ctx->fmap.data(), (const cxf *)ctx->band,
-                                        (const cxf *)ctx->dinv, BY,
-                                        BhYh, 0, m, ctx->Xn,
-                                        cs ? nullptr : ctx->Xhn, xns, 0, (cxf *)ctx->ysc, nullptr, ctx->s));
+    CKC(band_solve_sides<float, double>(n, ctx->klp, ctx->kup, ne, ctx->fmap.data(), (const cxf *)ctx->band,
+                                        (const cxf *)ctx->dinv, BY, BhYh, 0, m, ctx->Xn, cs ? nullptr : ctx->Xhn,
+                                        xns, 0, (cxf *)ctx->ysc, nullptr, ctx->s, tma_ptr(ctx), ctx->d_err));
     ev_end(ctx, ctx->ev_solve, k0);
     int g = launch_colnorm2(BY, m, m, n, ctx->colp, ctx->s);
     launch_reduce_parts(ctx->colp, g, m, ctx->bynorm2, ctx->s);
@@ -287,11 +293,11 @@ void do_filter(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, cxd *Q, cxd *Qh, 
       if (done) break;
       if (it + 1 < steps) {
         int ks = ev_begin(ctx, ctx->ev_solve);
-        CKC(band_solve_sides<float, float>(n, ctx->kl, ctx->ku, ne, ctx->fmap.data(), (const cxf *)ctx->band,
-                                           (const cxf *)ctx->dinv,
-                                           (const cxf *)ctx->Rn,
+        CKC(band_solve_sides<float, float>(n, ctx->klp, ctx->kup, ne, ctx->fmap.data(), (const cxf *)ctx->band,
+                                           (const cxf *)ctx->dinv, (const cxf *)ctx->Rn,
                                            cs ? nullptr : (const cxf *)ctx->Rhn, xns, m, ctx->Xn,
-                                           cs ? nullptr : ctx->Xhn, xns, 1, (cxf *)ctx->ysc, nullptr, ctx->s));
+                                           cs ? nullptr : ctx->Xhn, xns, 1, (cxf *)ctx->ysc, nullptr, ctx->s,
+                                           tma_ptr(ctx), ctx->d_err));
         ev_end(ctx, ctx->ev_solve, ks);
       }
     }
@@ -331,7 +337,6 @@ int do_rr(feast_nh_ctx *ctx, const cxd *Q, const cxd *Qh, int m, cxd *Y, cxd *Yh
   cudaStream_t s = ctx->s;
   const CsrView *Bp = ctx->hasB ? &ctx->B : nullptr;
   const CsrView *BHp = ctx->hasB ? &ctx->BH : nullptr;
-  CKC(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s));
   // 2.a  B_Q = Q^^H B Q
   const cxd *BQq = Q;
   if (ctx->hasB) {
@@ -539,6 +544,10 @@ feast_nh_status feast_nh_init(feast_nh_ctx **out, const feast_nh_csr *A, const f
     REQ(ext[2] == 0, "a column index of A or B is outside [0, n)");
     ctx->kl = ext[0];
     ctx->ku = ext[1];
+    // stored band: kl rounded up to even and kl+ku+1 even, so that band rows and
+    // the TMA box origins are 16-byte aligned (extra diagonals hold zeros)
+    ctx->klp = ctx->kl + (ctx->kl & 1);
+    ctx->kup = ctx->ku + ((ctx->klp + ctx->ku + 1) & 1);
     // Real pencil and a node set closed under conjugation (Sec. 2.4, Table
     // tab:solve): (conj(z) B - A) = conj(z B - A), so only one matrix of each
     // conjugate pair is factorised and the other uses the conjugated factors.
@@ -569,15 +578,24 @@ feast_nh_status feast_nh_init(feast_nh_ctx **out, const feast_nh_csr *A, const f
       CKC(cudaMemcpyAsync(ctx->dzf, zf.data(), ctx->nf * sizeof(cxd), cudaMemcpyHostToDevice, ctx->s));
     }
     const bool f32 = fp32(ctx);
-    const bool fits = f32 ? (band_fits<float>(ctx->kl, ctx->ku) && band_solve_fits<float>(ctx->kl, ctx->ku))
-                          : (band_fits<double>(ctx->kl, ctx->ku) && band_solve_fits<double>(ctx->kl, ctx->ku));
+    const bool fits = f32 ? (band_fits<float>(ctx->klp, ctx->kup) &&
+                             (band_tma_fits(ctx->klp, ctx->kup) || band_solve_fits<float>(ctx->klp, ctx->kup)))
+                          : (band_fits<double>(ctx->klp, ctx->kup) && band_solve_fits<double>(ctx->klp, ctx->kup));
     if (!fits) {
       char msg[160];
       std::snprintf(msg, sizeof msg, "band (kl=%d, ku=%d) too wide for the banded inner solver", ctx->kl, ctx->ku);
       REQ(false, msg);
     }
     const size_t es = f32 ? sizeof(cxf) : sizeof(cxd);
-    ctx->band = dalloc<void>(ctx, (size_t)ctx->nf * n * (ctx->kl + ctx->ku + 1) * es);
+    const size_t band_elems = (size_t)ctx->nf * n * (ctx->klp + ctx->kup + 1);
+    ctx->band = dalloc<void>(ctx, band_elems * es);
+    if (f32 && band_tma_fits(ctx->klp, ctx->kup)) {
+      ctx->bandT = dalloc<void>(ctx, band_elems * es);
+      ctx->tma.assign(band_tma_bytes(), 0);
+      if (!band_tma_make(ctx->tma.data(), n, ctx->klp, ctx->kup, ctx->nf, (const cxf *)ctx->band,
+                         (const cxf *)ctx->bandT))
+        ctx->tma.clear();
+    }
     const size_t yse = f32 ? band_solve_scratch_elems<float>(n, m0, ne) : band_solve_scratch_elems<double>(n, m0, ne);
     ctx->ysc = dalloc<void>(ctx, yse * es);
     if (f32) ctx->dinv = dalloc<void>(ctx, band_diag_inv_elems(n, ctx->nf) * sizeof(cxf));
@@ -661,6 +679,7 @@ feast_nh_status feast_nh_filter(feast_nh_ctx *ctx, const void *Y, const void *Yh
   try {
     REQ(Y && Q && Qh && m >= 1 && m <= ctx->m0, "filter: bad block pointers or m");
     REQ(cs_mode(ctx) || Yh, "filter: Yh is required unless the problem is complex symmetric");
+    CKC(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->s));
     do_filter(ctx, (const cxd *)Y, (const cxd *)Yh, (cxd *)Q, (cxd *)Qh, m);
   } catch (const Fail &f) {
     return f.st;
@@ -673,6 +692,7 @@ feast_nh_status feast_nh_rr(feast_nh_ctx *ctx, const void *Q, const void *Qh, in
   if (!ctx) return FEAST_NH_EINVAL;
   try {
     REQ(Q && Qh && lambda && Y && Yh && m_new && m >= 1 && m <= ctx->m0, "rr: bad arguments");
+    CKC(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->s));
     const int mt = do_rr(ctx, (const cxd *)Q, (const cxd *)Qh, m, (cxd *)Y, (cxd *)Yh);
     CKC(cudaMemcpyAsync(lambda, ctx->lam, (size_t)mt * sizeof(cxd), cudaMemcpyDeviceToDevice, ctx->s));
     read_status(ctx);
@@ -691,6 +711,10 @@ feast_nh_status feast_nh_rr(feast_nh_ctx *ctx, const void *Q, const void *Qh, in
     }
     int herr = 0;
     std::memcpy(&herr, ctx->h_small + 1, sizeof(int));
+    if (herr & DEVERR_TIMEOUT) {
+      ctx->err = "a bounded wait for a tile load in the triangular solves gave up";
+      return FEAST_NH_ETIMEOUT;
+    }
     if (herr & DEVERR_QR_NOCONV) {
       ctx->err = "reduced eigenproblem: QR iteration did not converge";
       return FEAST_NH_ECUDA;
@@ -711,6 +735,7 @@ feast_nh_status feast_nh_solve(feast_nh_ctx *ctx, const void *Y0, const void *Yh
     const int n = ctx->n, m0 = ctx->m0;
     cudaStream_t s = ctx->s;
     CKC(cudaEventRecord(ctx->ev[0], s));
+    CKC(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s));
     ctx->factored = false;  // each solve factorises afresh and keeps the factors for its iterations
     ctx->have_prev = 0;
     ev_harvest(ctx->ev_solve);
@@ -744,6 +769,10 @@ feast_nh_status feast_nh_solve(feast_nh_ctx *ctx, const void *Y0, const void *Yh
       t_rr += b;
       int herr = 0;
       std::memcpy(&herr, ctx->h_small + 1, sizeof(int));
+      if (herr & DEVERR_TIMEOUT) {
+        ctx->err = "a bounded wait for a tile load in the triangular solves gave up";
+        throw Fail{FEAST_NH_ETIMEOUT};
+      }
       if (herr & DEVERR_QR_NOCONV) {
         ctx->err = "reduced eigenproblem: QR iteration did not converge";
         throw Fail{FEAST_NH_ECUDA};

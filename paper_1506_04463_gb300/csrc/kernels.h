@@ -19,10 +19,19 @@ cudaError_t band_factor(int n, int kl, int ku, int ne, cx<T> *band, int *d_err, 
 // solution (mode 0) or has it added (mode 1).  Skipped when *skip != 0.
 // fmap (host, ne entries, NULL: identity): node j uses factor slot fmap[j] &
 // 0xffff, conjugated when bit 16 is set.
+// tma (FP32 only, may be NULL): tensor maps from band_tma_make; err: device
+// error word (DEVERR_TIMEOUT if a bounded wait gave up).
 template <typename T, typename Tin>
 cudaError_t band_solve_sides(int n, int kl, int ku, int ne, const int *fmap, const cx<T> *band, const cx<T> *dinv,
                              const cx<Tin> *rhsR, const cx<Tin> *rhsL, size_t rns, int m, cxd *XR, cxd *XL,
-                             size_t xns, int mode, cx<T> *ysc, const int *skip, cudaStream_t s);
+                             size_t xns, int mode, cx<T> *ysc, const int *skip, cudaStream_t s,
+                             const void *tma = nullptr, int *err = nullptr);
+// TMA tile loads for the FP32 solves: tensor maps of the band and of its
+// transpose (opaque buffer of band_tma_bytes()); false if not available.
+bool band_tma_fits(int klp, int kup);
+bool band_tma_make(void *tma_out, int n, int klp, int kup, int nslots, const cxf *band, const cxf *bandT);
+size_t band_tma_bytes();
+void launch_band_transpose(int n, int kl, int ku, int nslots, const cxf *B, cxf *Bt, cudaStream_t s);
 template <typename T> size_t band_solve_scratch_elems(int n, int m, int ne);
 // Inverses of the 16 x 16 diagonal blocks of L and U (FP32 solve path).
 template <typename T>
