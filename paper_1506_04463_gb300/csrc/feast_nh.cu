@@ -39,6 +39,7 @@ struct feast_nh_ctx {
   int kl = -1, ku = -1;     // band of (z B - A)
   int klp = 0, kup = 0;     // stored band widths (kl rounded up to even, kl+ku+1 even)
   void *bandT = nullptr;    // FP32: transposed factors for the conjugate-transpose solves
+  void *kwork = nullptr;    // BiCGStab workspace
   std::vector<unsigned char> tma;  // tensor maps of band and bandT (empty: no TMA path)
   int nf = 0;              // shifted matrices factorised (ne, or ne/2 with conjugate node pairs)
   std::vector<int> fmap;   // node -> factor slot | conjugate << 16
@@ -72,6 +73,7 @@ struct feast_nh_ctx {
   cudaEvent_t ev[6] = {};
   double t_factor = 0, inner_res = 0;
   int inner_steps = 0;
+  bool krylov_ok = true;
   EvPool ev_solve, ev_resid;
 };
 
@@ -196,8 +198,14 @@ const void *tma_ptr(const feast_nh_ctx *ctx) { return ctx->tma.empty() ? nullptr
 
 bool cs_mode(const feast_nh_ctx *ctx) { return ctx->o.problem == FEAST_NH_PROBLEM_COMPLEX_SYMMETRIC; }
 bool fp32(const feast_nh_ctx *ctx) { return ctx->o.precision == FEAST_NH_PREC_FP32_IR; }
+bool krylov(const feast_nh_ctx *ctx) { return ctx->o.inner_kind == FEAST_NH_INNER_BICGSTAB; }
 
 void factorize(feast_nh_ctx *ctx) {
+  if (krylov(ctx)) {
+    ctx->factored = true;
+    ctx->t_factor = 0;
+    return;
+  }
   const CsrView *Bp = ctx->hasB ? &ctx->B : nullptr;
   CKC(cudaEventRecord(ctx->ev[4], ctx->s));
   CKC(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->s));
@@ -244,7 +252,28 @@ void do_filter(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, cxd *Q, cxd *Qh, 
     }
   }
   const size_t xns = (size_t)n * m;
-  if (!fp32(ctx)) {
+  if (krylov(ctx)) {
+    // batched BiCGStab on every (node, column) system, then Q = sum_j w_j X_j
+    double rel_r = 0, rel_l = 0;
+    int kb = ev_begin(ctx, ctx->ev_solve);
+    const int it_r = krylov_bicgstab(ctx->A, Bp, ne, ctx->dz, ctx->dw, BY, m, ctx->m0, inner_tol, ctx->o.inner_max,
+                                     ctx->kwork, ctx->Xn, &rel_r, ctx->s);
+    ev_end(ctx, ctx->ev_solve, kb);
+    launch_multishift_residual<double>(ctx->A, Bp, ne, ctx->dz, ctx->dw, ctx->Xn, BY, nullptr, Q, nullptr, m, nullptr,
+                                       ctx->s);
+    int it_l = 0;
+    if (!cs) {
+      kb = ev_begin(ctx, ctx->ev_solve);
+      it_l = krylov_bicgstab(ctx->AH, BHp, ne, ctx->dzc, ctx->dwc, BhYh, m, ctx->m0, inner_tol, ctx->o.inner_max,
+                             ctx->kwork, ctx->Xhn, &rel_l, ctx->s);
+      ev_end(ctx, ctx->ev_solve, kb);
+      launch_multishift_residual<double>(ctx->AH, BHp, ne, ctx->dzc, ctx->dwc, ctx->Xhn, BhYh, nullptr, Qh, nullptr, m,
+                                         nullptr, ctx->s);
+    }
+    ctx->inner_steps = it_r > it_l ? it_r : it_l;
+    ctx->inner_res = rel_r > rel_l ? rel_r : rel_l;
+    ctx->krylov_ok = !(ctx->inner_res > inner_tol);
+  } else if (!fp32(ctx)) {
     int k = ev_begin(ctx, ctx->ev_solve);
     CKC(band_solve_sides<double, double>(n, ctx->klp, ctx->kup, ne, ctx->fmap.data(), (const cxd *)ctx->band, nullptr,
                                          BY, BhYh, 0, m,
@@ -491,7 +520,11 @@ feast_nh_status feast_nh_init(feast_nh_ctx **out, const feast_nh_csr *A, const f
     REQ(contour->kind != 2 || (contour->z && contour->w), "custom contour needs z and w");
     REQ(m0 >= 1 && m0 <= kMaxM0 && m0 <= A->n, "m0 must be in [1, min(128, n)]");
     if (opts) ctx->o = *opts; else feast_nh_default_opts(&ctx->o);
-    REQ(ctx->o.inner_kind == FEAST_NH_INNER_BANDED, "only the banded inner solver is available");
+    REQ(ctx->o.inner_kind == FEAST_NH_INNER_BANDED || ctx->o.inner_kind == FEAST_NH_INNER_BICGSTAB,
+        "inner_kind must be BANDED or BICGSTAB");
+    REQ(ctx->o.inner_kind != FEAST_NH_INNER_BICGSTAB || ctx->o.precision == FEAST_NH_PREC_FP64,
+        "the BiCGStab inner solver runs in FP64");
+    REQ(ctx->o.inner_max >= 1, "inner_max must be >= 1");
     REQ(ctx->o.precision == FEAST_NH_PREC_FP64 || ctx->o.precision == FEAST_NH_PREC_FP32_IR, "bad precision");
     REQ(ctx->o.problem == FEAST_NH_PROBLEM_GENERAL || ctx->o.problem == FEAST_NH_PROBLEM_COMPLEX_SYMMETRIC,
         "bad problem kind");
@@ -578,27 +611,30 @@ feast_nh_status feast_nh_init(feast_nh_ctx **out, const feast_nh_csr *A, const f
       CKC(cudaMemcpyAsync(ctx->dzf, zf.data(), ctx->nf * sizeof(cxd), cudaMemcpyHostToDevice, ctx->s));
     }
     const bool f32 = fp32(ctx);
-    const bool fits = f32 ? (band_fits<float>(ctx->klp, ctx->kup) &&
+    const bool fits = krylov(ctx) || (f32 ? (band_fits<float>(ctx->klp, ctx->kup) &&
                              (band_tma_fits(ctx->klp, ctx->kup) || band_solve_fits<float>(ctx->klp, ctx->kup)))
-                          : (band_fits<double>(ctx->klp, ctx->kup) && band_solve_fits<double>(ctx->klp, ctx->kup));
+                          : (band_fits<double>(ctx->klp, ctx->kup) && band_solve_fits<double>(ctx->klp, ctx->kup)));
     if (!fits) {
       char msg[160];
       std::snprintf(msg, sizeof msg, "band (kl=%d, ku=%d) too wide for the banded inner solver", ctx->kl, ctx->ku);
       REQ(false, msg);
     }
     const size_t es = f32 ? sizeof(cxf) : sizeof(cxd);
-    const size_t band_elems = (size_t)ctx->nf * n * (ctx->klp + ctx->kup + 1);
+    const size_t band_elems = krylov(ctx) ? 0 : (size_t)ctx->nf * n * (ctx->klp + ctx->kup + 1);
     ctx->band = dalloc<void>(ctx, band_elems * es);
-    if (f32 && band_tma_fits(ctx->klp, ctx->kup)) {
+    if (krylov(ctx)) ctx->kwork = dalloc<void>(ctx, krylov_work_bytes(n, m0, ne));
+    if (f32 && !krylov(ctx) && band_tma_fits(ctx->klp, ctx->kup)) {
       ctx->bandT = dalloc<void>(ctx, band_elems * es);
       ctx->tma.assign(band_tma_bytes(), 0);
       if (!band_tma_make(ctx->tma.data(), n, ctx->klp, ctx->kup, ctx->nf, (const cxf *)ctx->band,
                          (const cxf *)ctx->bandT))
         ctx->tma.clear();
     }
-    const size_t yse = f32 ? band_solve_scratch_elems<float>(n, m0, ne) : band_solve_scratch_elems<double>(n, m0, ne);
+    const size_t yse = krylov(ctx) ? 0
+                       : f32   ? band_solve_scratch_elems<float>(n, m0, ne)
+                               : band_solve_scratch_elems<double>(n, m0, ne);
     ctx->ysc = dalloc<void>(ctx, yse * es);
-    if (f32) ctx->dinv = dalloc<void>(ctx, band_diag_inv_elems(n, ctx->nf) * sizeof(cxf));
+    if (f32 && !krylov(ctx)) ctx->dinv = dalloc<void>(ctx, band_diag_inv_elems(n, ctx->nf) * sizeof(cxf));
     const size_t blk = (size_t)n * m0 * sizeof(cxd);
     ctx->Yw = dalloc<cxd>(ctx, blk);
     ctx->Yhw = dalloc<cxd>(ctx, blk);
@@ -681,6 +717,10 @@ feast_nh_status feast_nh_filter(feast_nh_ctx *ctx, const void *Y, const void *Yh
     REQ(cs_mode(ctx) || Yh, "filter: Yh is required unless the problem is complex symmetric");
     CKC(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->s));
     do_filter(ctx, (const cxd *)Y, (const cxd *)Yh, (cxd *)Q, (cxd *)Qh, m);
+    if (krylov(ctx) && !ctx->krylov_ok) {
+      ctx->err = "BiCGStab stopped at inner_max iterations above inner_tol (outputs hold the last iterate)";
+      return FEAST_NH_EINNER;
+    }
   } catch (const Fail &f) {
     return f.st;
   }
@@ -707,7 +747,7 @@ feast_nh_status feast_nh_rr(feast_nh_ctx *ctx, const void *Q, const void *Qh, in
       info->max_res = ctx->h_st->max_res;
       info->kl = ctx->kl;
       info->ku = ctx->ku;
-      info->n_factorizations = ctx->nf;
+      info->n_factorizations = krylov(ctx) ? 0 : ctx->nf;
     }
     int herr = 0;
     std::memcpy(&herr, ctx->h_small + 1, sizeof(int));
@@ -821,7 +861,7 @@ feast_nh_status feast_nh_solve(feast_nh_ctx *ctx, const void *Y0, const void *Yh
       info->t_resid_kernel_ms = ctx->ev_resid.ms;
       info->n_solve_launches = ctx->ev_solve.launches;
       info->n_resid_launches = ctx->ev_resid.launches;
-      info->n_factorizations = ctx->nf;
+      info->n_factorizations = krylov(ctx) ? 0 : ctx->nf;
     }
     if (!conv) {
       ctx->err = "no convergence within max_iter outer iterations";

@@ -70,6 +70,11 @@ void launch_reduce_parts(const double *parts, int nparts, int m, double *out, cu
 cudaError_t csr_transpose(const CsrView &A, int32_t *rowptr_t, int32_t *colind_t, double *val_t,
                           int32_t *work, cudaStream_t s);
 
+// ---------------- krylov.cu : batched BiCGStab ------------------------------
+size_t krylov_work_bytes(int n, int m0, int ne);
+int krylov_bicgstab(const CsrView &A, const CsrView *B, int ne, const cxd *d_z, const cxd *d_w, const cxd *BY, int m,
+                    int m0, double tol, int max_it, void *work, cxd *Xout, double *maxrel, cudaStream_t s);
+
 // ---------------- dense.cu : tall-skinny and small dense kernels -----------
 // G = X^H Y (mx x my), X: n x mx (ld ldx), Y: n x my (ld ldy); partial buffer
 // of size nchunks*mx*my complex.

@@ -207,3 +207,41 @@ def test_conjugate_pair_factorisation_count():
     ctx3 = make_ctx(wkc)
     out3 = ctx3.solve(dev(wkc.Y0), dev(wkc.Yh0))
     assert out3["info"]["n_factorizations"] == rows["complex_general"][0] * wkc.contour.ne
+
+
+# ---------------- batched BiCGStab inner solver ----------------
+def test_bicgstab_filter_matches_oracle():
+    wk = wl.config1("b")
+    ctx = make_ctx(wk, inner_kind=F.INNER_BICGSTAB, inner_max=4000, inner_tol=1e-12)
+    Q, Qh = ctx.filter(dev(wk.Y0), dev(wk.Yh0))
+    z, w = contour_nodes(wk.contour)
+    Qo, Qho = OF.contour_integration(wk.A, None, OF.node_solvers(wk.A, None, z, dense=False), z, w, wk.Y0, wk.Yh0)
+    assert np.max(np.abs(host(Q) - Qo)) < 1e-9 * np.max(np.abs(Qo))
+    assert np.max(np.abs(host(Qh) - Qho)) < 1e-9 * np.max(np.abs(Qho))
+
+
+@pytest.mark.parametrize("case", ["pencil", "tridiag"])
+def test_bicgstab_solve(case):
+    if case == "pencil":
+        wk = wl.pencil_workload(40, 3, ne=8, m0=8)
+        oo = OF.feast_nh(wk.A, wk.B, wk.contour, wk.m0, wk.Y0, wk.Yh0)
+        ref = oo["lam"]
+    else:
+        wk = wl.config1("b")
+        ref = wk.exact
+    ctx = make_ctx(wk, inner_kind=F.INNER_BICGSTAB, inner_max=4000, inner_tol=1e-12)
+    out = ctx.solve(dev(wk.Y0), dev(wk.Yh0))
+    assert out["status"] == F.OK and out["m"] == ref.size
+    assert match_rel(host(out["lam"]), ref, 1e-3) < 1e-9
+    invariants(wk, out)
+    assert out["info"]["inner_steps"] > 1 and out["info"]["n_factorizations"] == 0
+
+
+def test_bicgstab_reports_unconverged_interior_systems():
+    # interior nodes of the convection-diffusion operator: Krylov stalls and the
+    # filter reports FEAST_NH_EINNER (the banded direct solver handles these)
+    wk = wl.config2(N=30, m0=48, ne=16)
+    ctx = make_ctx(wk, inner_kind=F.INNER_BICGSTAB, inner_max=60, inner_tol=1e-12)
+    with pytest.raises(F.FeastError) as e:
+        ctx.filter(dev(wk.Y0), dev(wk.Yh0))
+    assert e.value.status == F.EINNER
