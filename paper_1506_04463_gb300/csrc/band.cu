@@ -1126,35 +1126,71 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
 }
 
 namespace kt {
-constexpr int NB = 16, R = 16, WARPS = 16, NT = 32 * WARPS, RED_LD = R + 1;
+constexpr int NB = 16, R = 16, WARPS = 16, NT = 32 * WARPS, OWNERS = R / 2, LSLD = NB + 1;
+// owner warps take DELTA fewer window rows each than the other warps, to make
+// room for the block solve they do at the start of every step
+constexpr int DELTA = 4;
 constexpr long long kSpinLimit = 1ll << 26;
 __host__ __device__ inline int ring_rows(int bw) { return ceil_div(bw + NB, NB) * NB; }
 __host__ __device__ inline size_t smem_bytes(int BX, int bwmax) {
-  return (size_t)(2 * 2 * NB * BX + 2 * 256 + ring_rows(bwmax) * R + WARPS * NB * RED_LD) * sizeof(cxf) +
+  return (size_t)(2 * 2 * NB * BX + 4 * 256 + 2 * NB * LSLD + ring_rows(bwmax) * R + 2 * WARPS * 256) *
+             sizeof(cxf) +
          2 * sizeof(uint64_t);
+}
+// conflict-free slot of partial sum (row, col) in a warp's 16 x 16 block, for
+// both the 4 x 4 lane grid that writes it and the 16-row column that reads it
+// ring rows keep column c at 4 (c & 3) + (c >> 2), so that the four columns
+// c, c + 4, c + 8, c + 12 a lane multiplies are one 32-byte run
+__host__ __device__ inline int rperm(int c) { return ((c & 3) << 2) | (c >> 2); }
+__device__ __forceinline__ int rsw(int row, int col) { return row * 16 + (col ^ (((row & 3) << 2) | (row >> 2))); }
+// acc += op(a) b and acc -= op(a) b, op = conj when NEG
+template <bool NEG> __device__ __forceinline__ void mac(cxf &acc, cxf a, cxf b) {
+  if constexpr (NEG)
+    cfma_cj(acc, a, b);
+  else
+    cfma(acc, a, b);
+}
+template <bool NEG> __device__ __forceinline__ void msc(cxf &acc, cxf a, cxf b) {
+  if constexpr (NEG) {
+    acc.re = fmaf(-a.re, b.re, acc.re);
+    acc.re = fmaf(-a.im, b.im, acc.re);
+    acc.im = fmaf(-a.re, b.im, acc.im);
+    acc.im = fmaf(a.im, b.re, acc.im);
+  } else {
+    cfms(acc, a, b);
+  }
 }
 }  // namespace kt
 
-template <bool HERM, typename Tin>
+// One CTA: one (node, side, 16 right-hand-side columns) system, forward then
+// backward sweep over 16-row blocks.  Step s solves block s of the sweep:
+//   y = rhs_s - P_s - Lsub_s x_{s-1},  x_s = D_s y,
+// where P_s is the product of the factor rows of block s with the solution
+// rows of its window older than block s-1, Lsub_s the factor entries of block
+// s in the columns of block s-1, and D_s the inverse of the diagonal block.
+// P_{s+1} and Lsub_{s+1} need nothing from block s, so all 16 warps compute
+// them during step s (split over window rows) while the 8 owner warps (one
+// thread per entry of the 16 x 16 block) first do the short block solve for
+// step s: one barrier per step, and the serial part overlaps the product.
+template <bool HERM, bool NEG, typename Tin>
 __device__ __forceinline__ void kt_body(int n, int klp, int kup, int BX, const CUtensorMap *tm, const cxf *Dv,
                                         const cx<Tin> *Rh, cxd *Xn, cxf *Ys, int m, int mode, int c0, int slot,
-                                        bool cj, int *err, unsigned char *smem_raw) {
+                                        int *err, unsigned char *smem_raw) {
   using namespace kt;
-  const float vsg = (HERM != cj) ? -1.f : 1.f;
   const int lw = HERM ? kup : klp;  // lower width of the band the tiles come from
   const int uw = HERM ? klp : kup;  // upper width
-  const int bwmax = max(lw, uw);
-  const int RB = ring_rows(bwmax);
+  const int RB = ring_rows(max(lw, uw));
   const int BOXE = NB * BX;
-  cxf *Mbuf = reinterpret_cast<cxf *>(smem_raw);                  // 2 buffers x 2 boxes x BOXE
-  cxf *dbuf = Mbuf + (size_t)4 * BOXE;                              // 2 x 256, p-major inverse
-  cxf *ring = dbuf + 512;                                           // RB x R
-  cxf *red = ring + (size_t)RB * R;                                 // WARPS x NB x RED_LD
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(red + (size_t)WARPS * NB * RED_LD);
+  cxf *Mbuf = reinterpret_cast<cxf *>(smem_raw);  // 2 stages x 2 boxes x BOXE
+  cxf *dbuf = Mbuf + (size_t)4 * BOXE;            // 4 stages x 256, p-major inverse
+  cxf *Lsub = dbuf + 4 * 256;                     // 2 x NB x LSLD
+  cxf *ring = Lsub + 2 * NB * LSLD;               // RB x R solution rows
+  cxf *red = ring + (size_t)RB * R;               // 2 x WARPS x 256 partial sums
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(red + (size_t)2 * WARPS * 256);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int rl = lane >> 2, cl = lane & 3;
-  const bool owner = warp < R / 2;
-  const int tc = 2 * (warp % (R / 2)) + (lane >> 4), tr = lane & 15;
+  const bool owner = warp < OWNERS;
+  const int tc = 2 * (warp % OWNERS) + (lane >> 4), tr = lane & 15;
   const int gc = c0 + tc;
   const bool cok = owner && gc < m;
   const int nblk = ceil_div(n, NB);
@@ -1162,12 +1198,11 @@ __device__ __forceinline__ void kt_body(int n, int klp, int kup, int BX, const C
   const unsigned full = 0xffffffffu;
   const uint32_t tx_bytes = (uint32_t)(2 * BOXE * sizeof(cxf) + 256 * sizeof(cxf));
 
-  auto issue = [&](int step) {
-    const bool f = step < nblk;
-    const int b = f ? step : 2 * nblk - 1 - step;
-    const int buf = step & 1;
-    cxf *dst = Mbuf + (size_t)buf * 2 * BOXE;
-    uint64_t *mb = &mbar[buf];
+  auto issue = [&](int j) {
+    const bool f = j < nblk;
+    const int b = f ? j : 2 * nblk - 1 - j;
+    cxf *dst = Mbuf + (size_t)(j & 1) * 2 * BOXE;
+    uint64_t *mb = &mbar[j & 1];
     // TMA box origins must be even (16-byte aligned); the forward tile starts 16
     // entries left of the band so that out-of-band entries come in as zeros
     const int x0 = f ? -NB : (lw & ~1);
@@ -1176,7 +1211,135 @@ __device__ __forceinline__ void kt_body(int n, int klp, int kup, int BX, const C
     mbar_expect_tx(mb, tx_bytes);
     tma_load_3d(dst, tm, x0, b * NB, slot, mb);
     tma_load_3d(dst + BOXE, tm, x0 + BX, b * NB, slot, mb);
-    bulk_load(dbuf + buf * 256, Dv + (size_t)b * 1024 + off, 256 * sizeof(cxf), mb);
+    bulk_load(dbuf + (j & 3) * 256, Dv + (size_t)b * 1024 + off, 256 * sizeof(cxf), mb);
+  };
+  bool timed_out = false;
+  int confirmed = -1;  // tiles [0, confirmed] have landed (as seen by this thread)
+  auto spin = [&](int j) -> bool {
+    long long spins = 0;
+    while (!mbar_try_wait(&mbar[j & 1], (uint32_t)((j >> 1) & 1))) {
+      if (++spins > kSpinLimit) return false;
+      if (spins > 32) __nanosleep(64);
+    }
+    return true;
+  };
+  auto wait_tile = [&](int j) {
+    if (timed_out) return;
+    if (spin(j)) {
+      confirmed = j;
+    } else {
+      timed_out = true;
+      atomicOr(err, DEVERR_TIMEOUT);
+    }
+  };
+  int issued = -1;  // thread 0: last tile issued
+  // right-hand side of step j for this owner thread (0 outside the system)
+  auto load_rhs = [&](int j) -> cxf {
+    const bool f = j < nblk;
+    const int b = f ? j : 2 * nblk - 1 - j;
+    const int r = b * NB + tr;
+    if (!(r < n && cok)) return mk(0.f, 0.f);
+    return f ? ccast<float>(Rh[(size_t)r * m + gc]) : Ys[(size_t)r * R + tc];
+  };
+  auto load_xold = [&](int j) -> cxd {
+    const int b = 2 * nblk - 1 - j;
+    const int r = b * NB + tr;
+    if (j < nblk || !mode || !(r < n && cok)) return mk(0.0, 0.0);
+    return Xn[(size_t)r * m + gc];
+  };
+  // Lsub_j and P_j for step j from its tile (stage j & 1)
+  auto prepare = [&](int j) {
+    const bool f = j < nblk;
+    const int b = f ? j : 2 * nblk - 1 - j;
+    const int kb = b * NB;
+    const cxf *Ms = Mbuf + (size_t)(j & 1) * 2 * BOXE;
+    cxf *Ls = Lsub + (j & 1) * NB * LSLD;
+    // band offset of (row kb + r, column i) relative to the box origin:
+    // forward tt = i - (kb + r) + lw + NB (origin -NB), backward
+    // tt = i - (kb + r) + (lw & 1) (origin lw rounded down to even)
+    const int tbase = f ? lw + NB - kb : (lw & 1) - kb;
+    if (tid >= NT - NB * NB) {  // non-owner warps
+      const int r = (tid - (NT - NB * NB)) >> 4, p = tid & 15;
+      const int i = f ? kb - NB + p : kb + NB + p;  // columns of the previous block of the sweep
+      const int d = i - (kb + r);
+      cxf v = mk(0.f, 0.f);
+      if (i >= 0 && i < n && (f ? d >= -lw : d <= uw)) {
+        const int tt = i + tbase - r;
+        v = Ms[r * BX + tt + (tt < BX ? 0 : BOXE - BX)];
+      }
+      Ls[r * LSLD + p] = v;
+    }
+    // window rows older than the previous block
+    int hlo, hhi;
+    if (f) {
+      hlo = max(0, kb - lw);
+      hhi = max(0, kb - NB);
+    } else {
+      hlo = kb + 2 * NB;
+      hhi = min(n, kb + NB + uw);
+    }
+    const int len = max(hhi - hlo, 0);
+    const int per_o = max(0, ceil_div(len + OWNERS * DELTA, WARPS) - DELTA);
+    const int per_n = ceil_div(len - OWNERS * per_o, WARPS - OWNERS);
+    const int wlo = owner ? hlo + warp * per_o : hlo + OWNERS * per_o + (warp - OWNERS) * per_n;
+    const int whi = min(hhi, wlo + (owner ? per_o : per_n));
+    cxf acc[2][4];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) acc[q][t] = mk(0.f, 0.f);
+    // Segments of [wlo, whi) on which every row of the tile reads the same box
+    // and the ring rows are contiguous: plain pointer walks there; the <= 15
+    // columns where rows straddle the two boxes pick the box per entry.
+    const int e0 = BX - tbase;  // rows r read box 1 from column e0 + r on
+    int a = wlo;
+    while (a < whi) {
+      const int rs = a % RB;
+      int b = min(whi, a + (RB - rs));
+      const int mode_ = a < e0 ? 0 : (a < e0 + NB - 1 ? 1 : 2);
+      b = min(b, mode_ == 0 ? e0 : (mode_ == 1 ? e0 + NB - 1 : b));
+      const cxf *py = ring + (size_t)rs * R + 4 * cl;
+      if (mode_ != 1) {
+        const int off = mode_ == 0 ? 0 : BOXE - BX;
+        const cxf *p0 = Ms + rl * BX + (a + tbase - rl) + off;
+        const cxf *p1 = Ms + (rl + 8) * BX + (a + tbase - rl - 8) + off;
+        const int cnt = b - a;
+#pragma unroll 4
+        for (int k = 0; k < cnt; ++k) {
+          const cxf mv0 = p0[k], mv1 = p1[k];
+          const float4 ya = *reinterpret_cast<const float4 *>(py + k * R);
+          const float4 yb = *reinterpret_cast<const float4 *>(py + k * R + 2);
+          const cxf yv[4] = {mk(ya.x, ya.y), mk(ya.z, ya.w), mk(yb.x, yb.y), mk(yb.z, yb.w)};
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            mac<NEG>(acc[0][t], mv0, yv[t]);
+            mac<NEG>(acc[1][t], mv1, yv[t]);
+          }
+        }
+      } else {
+        for (int i = a; i < b; ++i) {
+          cxf mv[2];
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int tt = i + tbase - (rl + 8 * q);
+            mv[q] = Ms[(rl + 8 * q) * BX + tt + (tt < BX ? 0 : BOXE - BX)];
+          }
+          const float4 ya = *reinterpret_cast<const float4 *>(py + (i - a) * R);
+          const float4 yb = *reinterpret_cast<const float4 *>(py + (i - a) * R + 2);
+          const cxf yv[4] = {mk(ya.x, ya.y), mk(ya.z, ya.w), mk(yb.x, yb.y), mk(yb.z, yb.w)};
+#pragma unroll
+          for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) mac<NEG>(acc[q][t], mv[q], yv[t]);
+        }
+      }
+      a = b;
+    }
+    cxf *rw = red + ((size_t)(j & 1) * WARPS + warp) * 256;
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) rw[rsw(rl + 8 * q, cl + 4 * t)] = acc[q][t];
   };
 
   if (tid == 0) {
@@ -1185,116 +1348,91 @@ __device__ __forceinline__ void kt_body(int n, int klp, int kup, int BX, const C
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncthreads();
-  if (tid == 0) issue(0);
-  bool timed_out = false;
-  for (int step = 0; step < nsteps; ++step) {
-    const bool fwd = step < nblk;
-    const int b = fwd ? step : 2 * nblk - 1 - step;
-    const int kb = b * NB;
-    const int nbk = min(NB, n - kb);
-    const int buf = step & 1;
-    const cxf *Ms = Mbuf + (size_t)buf * 2 * BOXE;
-    const cxf *dg = dbuf + buf * 256;
-    cxf acc2 = mk(0.f, 0.f);
-    {
-      const int r = kb + tr;
-      if (r < n && cok) acc2 = fwd ? ccast<float>(Rh[(size_t)r * m + gc]) : Ys[(size_t)r * R + tc];
-    }
-    if (!timed_out) {
-      long long spins = 0;
-      while (!mbar_try_wait(&mbar[buf], (uint32_t)((step >> 1) & 1))) {
-        if (++spins > kSpinLimit) {
-          timed_out = true;
-          atomicOr(err, DEVERR_TIMEOUT);
-          break;
-        }
-        if (spins > 32) __nanosleep(64);
-      }
-    }
-    __syncthreads();
-    if (tid == 0 && step + 1 < nsteps && !timed_out) {
+  if (tid == 0) {
+    issue(0);
+    issue(1);
+    issued = 1;
+  }
+  wait_tile(0);
+  prepare(0);
+  __syncthreads();
+  cxf rhs_next = owner ? load_rhs(0) : mk(0.f, 0.f);
+  cxd xold_next = mk(0.0, 0.0);
+  cxf xprev = mk(0.f, 0.f);
+  for (int s = 0; s < nsteps; ++s) {
+    if (tid == 0 && s + 2 < nsteps && !timed_out) {
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      issue(step + 1);
+      issue(s + 2);
+      issued = s + 2;
     }
-    // ---- GEMM over the rows already solved, split over warps ----
-    const int bw = fwd ? lw : uw;
-    int hlo, hhi;
-    if (fwd) {
-      hlo = max(0, kb - bw);
-      hhi = kb;
-    } else {
-      hlo = kb + nbk;
-      hhi = min(n, kb + nbk + bw);
-    }
-    const int len = max(hhi - hlo, 0);
-    const int per = ceil_div(len, WARPS);
-    const int wlo = hlo + warp * per, whi = min(hhi, wlo + per);
-    cxf acc[2][4];
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-#pragma unroll
-      for (int t = 0; t < 4; ++t) acc[q][t] = mk(0.f, 0.f);
-    if (wlo < whi) {
-      int rslot = wlo % RB;
-      // band offset of (row kb+rl+8q, column i) relative to the box origin:
-      // forward tt = i - r + lw + NB (origin -NB), backward tt = i - r + (lw & 1)
-      // (origin lw rounded down to even); always inside [0, 2 BX)
-      const int tbase = fwd ? lw + NB - kb : (lw & 1) - kb;
-#pragma unroll 4
-      for (int i = wlo; i < whi; ++i) {
-        cxf mv[2], yv[4];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int row = rl + 8 * q;
-          const int tt = i + tbase - row;
-          cxf v = Ms[row * BX + tt + (tt < BX ? 0 : BOXE - BX)];
-          v.im *= vsg;
-          mv[q] = v;
-        }
-#pragma unroll
-        for (int t = 0; t < 4; ++t) yv[t] = ring[rslot * R + cl + 4 * t];
-#pragma unroll
-        for (int q = 0; q < 2; ++q)
-#pragma unroll
-          for (int t = 0; t < 4; ++t) cfma(acc[q][t], mv[q], yv[t]);
-        if (++rslot == RB) rslot = 0;
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-#pragma unroll
-      for (int t = 0; t < 4; ++t) red[(warp * NB + rl + 8 * q) * RED_LD + cl + 4 * t] = acc[q][t];
-    __syncthreads();
     if (owner) {
-      cxf sum = mk(0.f, 0.f);
+      const bool fwd = s < nblk;
+      const int b = fwd ? s : 2 * nblk - 1 - s;
+      const int kb = b * NB;
+      const int nbk = min(NB, n - kb);
+      const cxf rhs = rhs_next;
+      const cxd xold = xold_next;
+      const cxf *rr = red + (size_t)(s & 1) * WARPS * 256 + rsw(tr, tc);
+      cxf psum[4];
 #pragma unroll
-      for (int w = 0; w < WARPS; ++w) sum = sum + red[(w * NB + tr) * RED_LD + tc];
-      acc2 = acc2 - sum;
-      // in-block solve: x = D acc, D the inverse of the diagonal block (p-major)
-      cxf x = mk(0.f, 0.f);
+      for (int w = 0; w < 4; ++w) psum[w] = rr[w * 256];
 #pragma unroll
-      for (int p = 0; p < NB; ++p) {
-        cxf a;
-        a.re = __shfl_sync(full, acc2.re, (lane & 16) | p);
-        a.im = __shfl_sync(full, acc2.im, (lane & 16) | p);
-        cxf dv = dg[p * NB + tr];
-        dv.im *= vsg;
-        cfma(x, dv, a);
+      for (int w = 4; w < WARPS; ++w) psum[w & 3] = psum[w & 3] + rr[w * 256];
+      cxf y = rhs - ((psum[0] + psum[1]) + (psum[2] + psum[3]));
+      const bool has_last = fwd ? s > 0 : s > nblk;
+      if (has_last) {
+        const cxf *Ls = Lsub + (s & 1) * NB * LSLD + tr * LSLD;
+#pragma unroll
+        for (int p = 0; p < NB; ++p) {
+          cxf a;
+          a.re = __shfl_sync(full, xprev.re, (lane & 16) | p);
+          a.im = __shfl_sync(full, xprev.im, (lane & 16) | p);
+          msc<NEG>(y, Ls[p], a);
+        }
       }
-      acc2 = x;
+      // in-block solve: x = D y, D the inverse of the diagonal block (p-major)
+      const cxf *dg = dbuf + (s & 3) * 256;
+      cxf x0 = mk(0.f, 0.f), x1 = mk(0.f, 0.f);
+#pragma unroll
+      for (int p = 0; p < NB; p += 2) {
+        cxf a0, a1;
+        a0.re = __shfl_sync(full, y.re, (lane & 16) | p);
+        a0.im = __shfl_sync(full, y.im, (lane & 16) | p);
+        a1.re = __shfl_sync(full, y.re, (lane & 16) | (p + 1));
+        a1.im = __shfl_sync(full, y.im, (lane & 16) | (p + 1));
+        mac<NEG>(x0, dg[p * NB + tr], a0);
+        mac<NEG>(x1, dg[(p + 1) * NB + tr], a1);
+      }
+      const cxf x = x0 + x1;
+      xprev = x;
       if (tr < nbk) {
         const int r = kb + tr;
-        ring[(r % RB) * R + tc] = acc2;
+        ring[(r % RB) * R + rperm(tc)] = x;
         if (fwd) {
-          Ys[(size_t)r * R + tc] = acc2;
+          Ys[(size_t)r * R + tc] = x;
         } else if (cok) {
-          cxd *xp = Xn + (size_t)r * m + gc;
-          const cxd vd = ccast<double>(acc2);
-          *xp = mode ? (*xp + vd) : vd;
+          const cxd vd = ccast<double>(x);
+          Xn[(size_t)r * m + gc] = mode ? (xold + vd) : vd;
         }
       }
+      // operands of the next step, after the stores above: the first backward
+      // step reads the rows the last forward step has just written
+      if (s + 1 < nsteps) {
+        rhs_next = load_rhs(s + 1);
+        xold_next = load_xold(s + 1);
+      }
     }
+    if (s + 1 < nsteps) {
+      wait_tile(s + 1);
+      prepare(s + 1);
+    }
+    __syncthreads();
   }
+  // after a timed-out wait, let the copies still in flight land (bounded)
+  // before the CTA's shared memory is released
+  if (tid == 0 && timed_out)
+    for (int j = confirmed + 1; j <= issued; ++j)
+      if (!spin(j)) break;
 }
 
 template <typename Tin>
@@ -1311,10 +1449,19 @@ __global__ void __launch_bounds__(kt::NT) k_band_solve_tma(int n, int klp, int k
   cxd *Xn = (side ? io.X[1] : io.X[0]) + (size_t)node * xns;
   cxf *Ys = ysc + (((size_t)side * gridDim.y + node) * gridDim.x + blockIdx.x) * (size_t)n * kt::R;
   const cxf *Dv = dinv + (size_t)slot * ceil_div(n, kt::NB) * 1024;
-  if (side)
-    kt_body<true, Tin>(n, klp, kup, tma.BX, &tma.tmBt, Dv, Rh, Xn, Ys, m, mode, c0, slot, cj, err, smem_raw);
-  else
-    kt_body<false, Tin>(n, klp, kup, tma.BX, &tma.tmB, Dv, Rh, Xn, Ys, m, mode, c0, slot, cj, err, smem_raw);
+  // the conjugate-transpose side reads conj(factor) entries; a conjugate node
+  // reads conj of its partner's factors; both together cancel
+  if (side) {
+    if (cj)
+      kt_body<true, false, Tin>(n, klp, kup, tma.BX, &tma.tmBt, Dv, Rh, Xn, Ys, m, mode, c0, slot, err, smem_raw);
+    else
+      kt_body<true, true, Tin>(n, klp, kup, tma.BX, &tma.tmBt, Dv, Rh, Xn, Ys, m, mode, c0, slot, err, smem_raw);
+  } else {
+    if (cj)
+      kt_body<false, true, Tin>(n, klp, kup, tma.BX, &tma.tmB, Dv, Rh, Xn, Ys, m, mode, c0, slot, err, smem_raw);
+    else
+      kt_body<false, false, Tin>(n, klp, kup, tma.BX, &tma.tmB, Dv, Rh, Xn, Ys, m, mode, c0, slot, err, smem_raw);
+  }
 }
 
 // Tensor maps of a band array (slots x n x W, 8-byte entries) for TMA loads of
