@@ -310,22 +310,51 @@ __device__ void block_reduce_sum2(double &a, double *red) {
   __syncthreads();
 }
 
-// work layout: H (m*m), Z (m*m), E (m*m)
-__global__ void __launch_bounds__(256) k_small_eig(const cxd *A, int m, cxd *lam, cxd *V, cxd *work, int *err) {
+// work layout: H (m*m; used when H does not fit in shared memory), Z (m*m), E (m*m).
+// H lives in dynamic shared memory (odd row stride) when it fits.  The QR
+// sweeps are explicit single-shift steps: the left rotations are formed and
+// applied by one warp, each lane owning the columns j = lane (mod 32), so a
+// rotation needs no block barrier; the right rotations of the whole sweep are
+// then applied row by row (rows are independent) to H and to Z.
+__device__ __forceinline__ void givens(cxd a, cxd b, double &c, cxd &s) {
+  // (c, s) with c real, c^2 + |s|^2 = 1 and [c s; -conj(s) c] [a; b] = [r; 0]
+  const double sc = fmax(fmax(fabs(a.re), fabs(a.im)), fmax(fabs(b.re), fabs(b.im)));
+  if (sc == 0.0) {
+    c = 1.0;
+    s = mk(0.0, 0.0);
+    return;
+  }
+  const double inv = 1.0 / sc;
+  const cxd as = inv * a, bs = inv * b;
+  const double aa2 = abs2(as), t = aa2 + abs2(bs);
+  const double rr = rsqrt(t);
+  if (aa2 == 0.0) {
+    c = 0.0;
+    s = mk(bs.re * rr, -bs.im * rr);
+    return;
+  }
+  const double ra = rsqrt(aa2);
+  c = aa2 * ra * rr;
+  s = (ra * rr) * (as * conj(bs));
+}
+
+__global__ void __launch_bounds__(256) k_small_eig(const cxd *A, int m, cxd *lam, cxd *V, cxd *work, int *err,
+                                                   int hsm) {
+  extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ cxd v[kMaxM0];
-  __shared__ cxd u[kMaxM0];
   __shared__ double red[256];
-  __shared__ cxd gc[kMaxM0];  // rotation sines
-  __shared__ double gcc[kMaxM0];
+  __shared__ cxd gs[kMaxM0];  // rotation sines of the current sweep
+  __shared__ double gcs[kMaxM0];
   __shared__ int sh_l, sh_hi, sh_done;
   __shared__ cxd sh_mu;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  cxd *H = work;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+  const int ld = hsm ? (m | 1) : m;
+  cxd *H = hsm ? reinterpret_cast<cxd *>(dsm) : work;
   cxd *Z = work + (size_t)m * m;
   cxd *E = work + 2 * (size_t)m * m;
   for (int e = tid; e < m * m; e += nt) {
-    H[e] = A[e];
-    int i = e / m, j = e - i * m;
+    const int i = e / m, j = e - i * m;
+    H[(size_t)i * ld + j] = A[e];
     Z[e] = mk(i == j ? 1.0 : 0.0, 0.0);
   }
   __syncthreads();
@@ -333,48 +362,54 @@ __global__ void __launch_bounds__(256) k_small_eig(const cxd *A, int m, cxd *lam
   for (int k = 0; k + 2 < m; ++k) {
     const int L = m - k - 1;
     double nrm2 = 0.0;
-    for (int i = tid; i < L; i += nt) nrm2 += abs2(H[(size_t)(k + 1 + i) * m + k]);
+    for (int i = tid; i < L; i += nt) nrm2 += abs2(H[(size_t)(k + 1 + i) * ld + k]);
     block_reduce_sum2(nrm2, red);
+    if (nrm2 == 0.0) continue;
     const double nrm = sqrt(nrm2);
-    if (nrm == 0.0) continue;
-    const cxd x0 = H[(size_t)(k + 1) * m + k];
+    const cxd x0 = H[(size_t)(k + 1) * ld + k];
     const double ax0 = cabs(x0);
     const cxd ph = ax0 > 0 ? mk(x0.re / ax0, x0.im / ax0) : mk(1.0, 0.0);
     const cxd beta = mk(-ph.re * nrm, -ph.im * nrm);
-    for (int i = tid; i < L; i += nt) v[i] = H[(size_t)(k + 1 + i) * m + k];
+    for (int i = tid; i < L; i += nt) v[i] = H[(size_t)(k + 1 + i) * ld + k];
     __syncthreads();
     if (tid == 0) v[0] = v[0] - beta;
     __syncthreads();
-    double vn2 = 0.0;
-    for (int i = tid; i < L; i += nt) vn2 += abs2(v[i]);
-    block_reduce_sum2(vn2, red);
+    // |v|^2 = nrm2 - |x0|^2 + |x0 - beta|^2
+    const double vn2 = nrm2 - abs2(x0) + abs2(x0 - beta);
     if (vn2 == 0.0) continue;
     const double sc = 2.0 / vn2;
-    // left: rows k+1.., columns k..m-1
-    for (int j = k + tid; j < m; j += nt) {
+    // left: H[k+1.., j] -= v (v^H H[k+1.., j]) sc, four threads per column
+    for (int base = 0; base < m - k; base += nt >> 2) {  // uniform trip count: all lanes shuffle
+      const int jj = base + (tid >> 2), j = k + jj, part = tid & 3;
+      const bool act = jj < m - k;
       cxd w = mk(0.0, 0.0);
-      for (int i = 0; i < L; ++i) cfma_cj(w, v[i], H[(size_t)(k + 1 + i) * m + j]);
+      if (act)
+        for (int i = part; i < L; i += 4) cfma_cj(w, v[i], H[(size_t)(k + 1 + i) * ld + j]);
+      w.re += __shfl_xor_sync(0xffffffffu, w.re, 1);
+      w.im += __shfl_xor_sync(0xffffffffu, w.im, 1);
+      w.re += __shfl_xor_sync(0xffffffffu, w.re, 2);
+      w.im += __shfl_xor_sync(0xffffffffu, w.im, 2);
       w = sc * w;
-      for (int i = 0; i < L; ++i) cfms(H[(size_t)(k + 1 + i) * m + j], v[i], w);
+      if (act)
+        for (int i = part; i < L; i += 4) cfms(H[(size_t)(k + 1 + i) * ld + j], v[i], w);
     }
     __syncthreads();
-    // right: all rows, columns k+1..; and Z
+    // right: every row of H and of Z, columns k+1..
     for (int r = tid; r < 2 * m; r += nt) {
-      cxd *M = r < m ? H : Z;
-      const int rr = r < m ? r : r - m;
+      cxd *M = r < m ? H + (size_t)r * ld : Z + (size_t)(r - m) * m;
       cxd s = mk(0.0, 0.0);
-      for (int i = 0; i < L; ++i) cfma(s, M[(size_t)rr * m + k + 1 + i], v[i]);
+      for (int i = 0; i < L; ++i) cfma(s, M[k + 1 + i], v[i]);
       s = sc * s;
       for (int i = 0; i < L; ++i) {
-        cxd &h = M[(size_t)rr * m + k + 1 + i];
+        cxd &h = M[k + 1 + i];
         // h -= s * conj(v_i)
         h.re -= s.re * v[i].re + s.im * v[i].im;
         h.im -= s.im * v[i].re - s.re * v[i].im;
       }
     }
     __syncthreads();
-    for (int i = 1 + tid; i < L; i += nt) H[(size_t)(k + 1 + i) * m + k] = mk(0.0, 0.0);
-    if (tid == 0) H[(size_t)(k + 1) * m + k] = beta;
+    for (int i = 1 + tid; i < L; i += nt) H[(size_t)(k + 1 + i) * ld + k] = mk(0.0, 0.0);
+    if (tid == 0) H[(size_t)(k + 1) * ld + k] = beta;
     __syncthreads();
   }
   // ---- shifted QR iteration to upper triangular (Schur) form ----
@@ -387,32 +422,32 @@ __global__ void __launch_bounds__(256) k_small_eig(const cxd *A, int m, cxd *lam
   const int maxtotal = 40 * m;
   while (true) {
     if (tid == 0) {
-      int hi = sh_hi;
+      const int hi = sh_hi;
       int l = hi;
       while (l > 0) {
-        double s = cabs1(H[(size_t)(l - 1) * m + l - 1]) + cabs1(H[(size_t)l * m + l]);
-        double sub = cabs1(H[(size_t)l * m + l - 1]);
+        const double s = cabs1(H[(size_t)(l - 1) * ld + l - 1]) + cabs1(H[(size_t)l * ld + l]);
+        const double sub = cabs1(H[(size_t)l * ld + l - 1]);
         if (sub <= DBL_EPSILON * s || sub < 1e-300) break;
         --l;
       }
-      if (l > 0) H[(size_t)l * m + l - 1] = mk(0.0, 0.0);
+      if (l > 0) H[(size_t)l * ld + l - 1] = mk(0.0, 0.0);
       sh_l = l;
       if (l == hi) {
         sh_hi = hi - 1;
-        its = -1;  // signal deflation
+        its = 0;
       } else {
         ++its;
         ++total;
-        const cxd a = H[(size_t)(hi - 1) * m + hi - 1], b = H[(size_t)(hi - 1) * m + hi];
-        const cxd c = H[(size_t)hi * m + hi - 1], d = H[(size_t)hi * m + hi];
+        const cxd a = H[(size_t)(hi - 1) * ld + hi - 1], b = H[(size_t)(hi - 1) * ld + hi];
+        const cxd c = H[(size_t)hi * ld + hi - 1], d = H[(size_t)hi * ld + hi];
         cxd mu;
         if (its % 11 == 10) {
           mu = d + mk(0.75 * cabs1(c), 0.0);
         } else {
-          cxd half = mk(0.5 * (a.re - d.re), 0.5 * (a.im - d.im));
-          cxd disc = csqrt(half * half + b * c);
-          cxd mid = mk(0.5 * (a.re + d.re), 0.5 * (a.im + d.im));
-          cxd m1 = mid + disc, m2 = mid - disc;
+          const cxd half = mk(0.5 * (a.re - d.re), 0.5 * (a.im - d.im));
+          const cxd disc = csqrt(half * half + b * c);
+          const cxd mid = mk(0.5 * (a.re + d.re), 0.5 * (a.im + d.im));
+          const cxd m1 = mid + disc, m2 = mid - disc;
           mu = abs2(m1 - d) < abs2(m2 - d) ? m1 : m2;
         }
         sh_mu = mu;
@@ -426,75 +461,68 @@ __global__ void __launch_bounds__(256) k_small_eig(const cxd *A, int m, cxd *lam
     __syncthreads();
     if (sh_done) break;
     const int l = sh_l, hi = sh_hi;
-    if (its < 0) {  // deflated (thread 0 state); resync its
-      its = 0;
-    }
     if (l >= hi) {
       __syncthreads();
       continue;
     }
     const cxd mu = sh_mu;
-    for (int i = l + tid; i <= hi; i += nt) H[(size_t)i * m + i] = H[(size_t)i * m + i] - mu;
+    for (int i = l + tid; i <= hi; i += nt) H[(size_t)i * ld + i] = H[(size_t)i * ld + i] - mu;
     __syncthreads();
-    for (int k = l; k < hi; ++k) {
-      if (tid == 0) {
-        const cxd a = H[(size_t)k * m + k], b = H[(size_t)(k + 1) * m + k];
-        const double aa = cabs(a), bb = cabs(b);
-        const double rho = hypot(aa, bb);
-        double c;
-        cxd s;
-        if (rho == 0.0) {
-          c = 1.0;
-          s = mk(0.0, 0.0);
-        } else if (aa == 0.0) {
-          c = 0.0;
-          s = mk(b.re / bb, -b.im / bb);
-        } else {
-          c = aa / rho;
-          cxd ph = mk(a.re / aa, a.im / aa);
-          s = (1.0 / rho) * (ph * conj(b));
+    // left rotations: warp 0, lane = owner of columns j = lane (mod 32)
+    if (tid < 32) {
+      for (int k = l; k < hi; ++k) {
+        const int ok = k & 31;
+        double c = 1.0;
+        cxd s = mk(0.0, 0.0);
+        if (lane == ok) {
+          givens(H[(size_t)k * ld + k], H[(size_t)(k + 1) * ld + k], c, s);
+          gcs[k] = c;
+          gs[k] = s;
         }
-        gcc[k] = c;
-        gc[k] = s;
-      }
-      __syncthreads();
-      const double c = gcc[k];
-      const cxd s = gc[k];
-      for (int j = k + tid; j < m; j += nt) {
-        const cxd h1 = H[(size_t)k * m + j], h2 = H[(size_t)(k + 1) * m + j];
-        H[(size_t)k * m + j] = c * h1 + s * h2;
-        H[(size_t)(k + 1) * m + j] = c * h2 - conj(s) * h1;
-      }
-      __syncthreads();
-    }
-    for (int k = l; k < hi; ++k) {
-      const double c = gcc[k];
-      const cxd s = gc[k];
-      const int rmax = min(k + 2, hi);
-      for (int r = tid; r < m + rmax + 1; r += nt) {
-        cxd *M;
-        int rr;
-        if (r <= rmax) {
-          M = H;
-          rr = r;
-        } else {
-          M = Z;
-          rr = r - rmax - 1;
+        c = __shfl_sync(0xffffffffu, c, ok);
+        s.re = __shfl_sync(0xffffffffu, s.re, ok);
+        s.im = __shfl_sync(0xffffffffu, s.im, ok);
+        for (int j = k + ((lane - k) & 31); j < m; j += 32) {
+          cxd *p1 = H + (size_t)k * ld + j, *p2 = p1 + ld;
+          const cxd h1 = *p1, h2 = *p2;
+          *p1 = c * h1 + s * h2;
+          *p2 = c * h2 - conj(s) * h1;
         }
-        const cxd h1 = M[(size_t)rr * m + k], h2 = M[(size_t)rr * m + k + 1];
-        M[(size_t)rr * m + k] = c * h1 + conj(s) * h2;
-        M[(size_t)rr * m + k + 1] = c * h2 - s * h1;
       }
-      __syncthreads();
     }
-    for (int i = l + tid; i <= hi; i += nt) H[(size_t)i * m + i] = H[(size_t)i * m + i] + mu;
+    __syncthreads();
+    // right rotations of the sweep: H rows 0..hi (row r meets rotations
+    // k >= r - 2) and all rows of Z, each row carried through k in order
+    for (int r = tid; r <= hi + m; r += nt) {
+      cxd *M;
+      int k0;
+      if (r <= hi) {
+        M = H + (size_t)r * ld;
+        k0 = max(l, r - 2);
+      } else {
+        M = Z + (size_t)(r - hi - 1) * m;
+        k0 = l;
+      }
+      if (k0 >= hi) continue;
+      cxd h1 = M[k0];
+      for (int k = k0; k < hi; ++k) {
+        const double c = gcs[k];
+        const cxd s = gs[k];
+        const cxd h2 = M[k + 1];
+        M[k] = c * h1 + conj(s) * h2;
+        h1 = c * h2 - s * h1;
+      }
+      M[hi] = h1;
+    }
+    __syncthreads();
+    for (int i = l + tid; i <= hi; i += nt) H[(size_t)i * ld + i] = H[(size_t)i * ld + i] + mu;
     __syncthreads();
   }
   // ---- eigenvectors of the triangular T = H, then V = Z E ----
   double tnorm = 0.0;
   for (int e = tid; e < m * m; e += nt) {
-    int i = e / m, j = e - i * m;
-    if (j >= i) tnorm = fmax(tnorm, cabs1(H[e]));
+    const int i = e / m, j = e - i * m;
+    if (j >= i) tnorm = fmax(tnorm, cabs1(H[(size_t)i * ld + j]));
   }
   red[tid] = tnorm;
   __syncthreads();
@@ -505,13 +533,13 @@ __global__ void __launch_bounds__(256) k_small_eig(const cxd *A, int m, cxd *lam
   const double small = fmax(red[0], 1e-300) * DBL_EPSILON;
   __syncthreads();
   for (int k = tid; k < m; k += nt) {
-    const cxd tk = H[(size_t)k * m + k];
+    const cxd tk = H[(size_t)k * ld + k];
     for (int j = k + 1; j < m; ++j) E[(size_t)j * m + k] = mk(0.0, 0.0);
     E[(size_t)k * m + k] = mk(1.0, 0.0);
     for (int j = k - 1; j >= 0; --j) {
       cxd s = mk(0.0, 0.0);
-      for (int l2 = j + 1; l2 <= k; ++l2) cfma(s, H[(size_t)j * m + l2], E[(size_t)l2 * m + k]);
-      cxd d = H[(size_t)j * m + j] - tk;
+      for (int l2 = j + 1; l2 <= k; ++l2) cfma(s, H[(size_t)j * ld + l2], E[(size_t)l2 * m + k]);
+      cxd d = H[(size_t)j * ld + j] - tk;
       if (cabs1(d) < small) d = mk(small, 0.0);
       E[(size_t)j * m + k] = -cdiv(s, d);
     }
@@ -519,7 +547,7 @@ __global__ void __launch_bounds__(256) k_small_eig(const cxd *A, int m, cxd *lam
   }
   __syncthreads();
   for (int e = tid; e < m * m; e += nt) {
-    int i = e / m, k = e - i * m;
+    const int i = e / m, k = e - i * m;
     cxd s = mk(0.0, 0.0);
     for (int l2 = 0; l2 <= k; ++l2) cfma(s, Z[(size_t)i * m + l2], E[(size_t)l2 * m + k]);
     V[e] = s;
@@ -534,6 +562,15 @@ __global__ void __launch_bounds__(256) k_small_eig(const cxd *A, int m, cxd *lam
 }
 
 void small_eig(const cxd *A, int m, cxd *lam, cxd *V, cxd *work, int *d_err, cudaStream_t s) {
-  k_small_eig<<<1, 256, 0, s>>>(A, m, lam, V, work, d_err);
+  const size_t hbytes = (size_t)m * (m | 1) * sizeof(cxd);
+  const int hsm = hbytes <= 200 * 1024;
+  if (hsm) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_small_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr = true;
+    }
+  }
+  k_small_eig<<<1, 256, hsm ? hbytes : 0, s>>>(A, m, lam, V, work, d_err, hsm);
   note_launch();
 }
