@@ -177,23 +177,31 @@ __global__ void __launch_bounds__(256) k_band_panel(int n, int kl, int ku, int k
 }
 
 // Register panel elimination with compile-time column indices: thread i holds
-// row i of the panel in row[]; prow_s is a double-buffered pivot row.
+// row i of the panel in row[]; prow_s is a double-buffered pivot row and
+// pinv_s the reciprocal of its pivot, formed once by the pivot thread.
 template <typename T, int NB>
-__device__ __forceinline__ void panel_eliminate(cx<T> (&row)[NB], cx<T> (*prow_s)[NB], int i, bool own, int nb,
-                                                int kl, int *err) {
+__device__ __forceinline__ void panel_eliminate(cx<T> (&row)[NB], cx<T> (*prow_s)[NB], cx<T> *pinv_s, int i, bool own,
+                                                int nb, int kl, int *err) {
 #pragma unroll
   for (int p = 0; p < NB; ++p) {
     if (p < nb) {
       cx<T> *pr = prow_s[p & 1];
       if (i == p) {
 #pragma unroll
-        for (int q = p; q < NB; ++q) pr[q] = row[q];
+        for (int q = p + 1; q < NB; ++q) pr[q] = row[q];
+        const cx<T> piv = row[p];
+        const T sc = fmax(fabs(piv.re), fabs(piv.im));
+        if (sc == 0) {
+          atomicOr(err, DEVERR_ZERO_PIVOT);
+          pinv_s[p & 1] = mk<T>(0, 0);
+        } else {
+          const T ar = piv.re / sc, ai = piv.im / sc, den = (ar * ar + ai * ai) * sc;
+          pinv_s[p & 1] = mk<T>(ar / den, -ai / den);
+        }
       }
       __syncthreads();
       if (own && i > p && i - p <= kl) {
-        const cx<T> piv = pr[p];
-        if (piv.re == 0 && piv.im == 0) atomicOr(err, DEVERR_ZERO_PIVOT);
-        const cx<T> l = cdiv(row[p], piv);
+        const cx<T> l = row[p] * pinv_s[p & 1];
         row[p] = l;
 #pragma unroll
         for (int q = p + 1; q < NB; ++q) cfms(row[q], l, pr[q]);
@@ -210,6 +218,7 @@ template <typename T, int NB>
 __global__ void __launch_bounds__(512) k_band_panel_reg(int n, int kl, int ku, int k, cx<T> *band, size_t ns,
                                                          int *err) {
   __shared__ cx<T> prow_s[2][NB];
+  __shared__ cx<T> pinv_s[2];
   const int W = kl + ku + 1;
   cx<T> *Bd = band + (size_t)blockIdx.x * ns;
   const int nb = min(NB, n - k);
@@ -222,7 +231,7 @@ __global__ void __launch_bounds__(512) k_band_panel_reg(int n, int kl, int ku, i
     const int d = q - i;
     row[q] = (own && q < nb && d >= -kl && d <= ku) ? Bd[(size_t)(k + i) * W + (d + kl)] : mk<T>(0, 0);
   }
-  panel_eliminate<T, NB>(row, prow_s, i, own, nb, kl, err);
+  panel_eliminate<T, NB>(row, prow_s, pinv_s, i, own, nb, kl, err);
   if (own) {
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
@@ -326,18 +335,19 @@ __global__ void __launch_bounds__(256) k_band_update(int n, int kl, int ku, int 
 }
 
 // ---------------------------------------------------------------------------
-// factorisation as one persistent launch: one thread-block cluster of FCL CTAs
+// factorisation as one persistent launch: one thread-block cluster of CL CTAs
 // per node.  Step k (columns [k, k+nb)): the CTA owning the panel factors it
 // in registers (thread = row); cluster barrier; every CTA forms U12 for the
-// 16-column groups it owns (group g belongs to CTA g mod FCL) and applies
+// 16-column groups it owns (group g belongs to CTA g mod CL; one warp per
+// column, lane = row, the solved entries passed on by shuffles) and applies
 // the rank-nb update to its columns of the trailing window; cluster barrier.
 // Band data shared between CTAs is read with ld.global.cg (L2), so no CTA can
-// see a stale L1 line.  Requires nb + kl <= 512 and ku <= 480.
+// see a stale L1 line.  Requires nb + kl <= 512 and ku small enough for the
+// owned columns of a CTA to fit FMAXC.
 // ---------------------------------------------------------------------------
-constexpr int FCL = 8;       // CTAs per cluster
 constexpr int FNT = 512;     // threads per CTA
 constexpr int FGW = 16;      // column-group width
-constexpr int FMAXC = 64;    // columns a CTA owns per step (ku <= 480)
+constexpr int FMAXC = 64;    // columns a CTA owns per step
 constexpr int FRC = 64;      // rows of L21 staged per chunk
 
 template <typename T>
@@ -351,8 +361,8 @@ __device__ __forceinline__ cx<T> ldcg(const cx<T> *p) {
   }
 }
 
-template <typename T, int NB>
-__global__ void __cluster_dims__(FCL, 1, 1) __launch_bounds__(FNT)
+template <typename T, int NB, int CL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(FNT)
     k_band_factor_cluster(int n, int kl, int ku, cx<T> *band, size_t ns, int *err) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
@@ -360,6 +370,7 @@ __global__ void __cluster_dims__(FCL, 1, 1) __launch_bounds__(FNT)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T> *Ls = reinterpret_cast<cx<T> *>(smem_raw);  // kl x NB: L21 of the current step
   __shared__ cx<T> prow_s[2][NB];
+  __shared__ cx<T> pinv_s[2];
   __shared__ cx<T> L11[NB][NB + 1];
   __shared__ cx<T> Us[NB][FMAXC];
   __shared__ int mycol[FMAXC];
@@ -369,7 +380,7 @@ __global__ void __cluster_dims__(FCL, 1, 1) __launch_bounds__(FNT)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int k = 0; k < n; k += NB) {
     const int nb = min(NB, n - k);
-    const int owner = (k / NB) % FCL;
+    const int owner = (k / NB) % CL;
     // ---------------- panel (owner CTA) ----------------
     if (rank == owner) {
       const int prow = min(n - k, nb + kl);
@@ -381,7 +392,7 @@ __global__ void __cluster_dims__(FCL, 1, 1) __launch_bounds__(FNT)
         const int d = q - i;
         row[q] = (own && q < nb && d >= -kl && d <= ku) ? ldcg(Bd + (size_t)(k + i) * W + (d + kl)) : mk<T>(0, 0);
       }
-      panel_eliminate<T, NB>(row, prow_s, i, own, nb, kl, err);
+      panel_eliminate<T, NB>(row, prow_s, pinv_s, i, own, nb, kl, err);
       if (own) {
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
@@ -398,8 +409,8 @@ __global__ void __cluster_dims__(FCL, 1, 1) __launch_bounds__(FNT)
       // owned columns: slot t -> group g0 + 8*(t/16), column 16g + t%16 (or -1)
       if (tid < FMAXC) {
         int g0 = c_beg / FGW;
-        g0 += ((rank - g0) % FCL + FCL) % FCL;
-        const int c = (g0 + FCL * (tid / FGW)) * FGW + tid % FGW;
+        g0 += ((rank - g0) % CL + CL) % CL;
+        const int c = (g0 + CL * (tid / FGW)) * FGW + tid % FGW;
         mycol[tid] = (c >= c_beg && c < c_end) ? c : -1;
       }
       for (int e = tid; e < NB * NB; e += FNT) {
@@ -412,25 +423,24 @@ __global__ void __cluster_dims__(FCL, 1, 1) __launch_bounds__(FNT)
         Ls[e] = (p < nb && r - (k + p) <= kl) ? ldcg(Bd + (size_t)r * W + (k + p - r + kl)) : mk<T>(0, 0);
       }
       __syncthreads();
-      // U12 = L11^{-1} A12, one owned column per thread
-      if (tid < FMAXC && mycol[tid] >= 0) {
-        const int c = mycol[tid];
-        cx<T> u[NB];
+      // U12 = L11^{-1} A12, one warp per owned column, lane = row
+      static_assert(sizeof(T) != 4 || NB == 32, "one lane per panel row");
+      for (int slot = warp; slot < FMAXC; slot += FNT / 32) {
+        const int c = mycol[slot];
+        if (c < 0) continue;
+        const int r = lane;
+        const int d = c - (k + r);
+        const bool in = r < nb && d <= ku;
+        cx<T> u = in ? ldcg(Bd + (size_t)(k + r) * W + (d + kl)) : mk<T>(0, 0);
 #pragma unroll
-        for (int r = 0; r < NB; ++r) {
-          const int d = c - (k + r);
-          u[r] = (r < nb && d <= ku) ? ldcg(Bd + (size_t)(k + r) * W + (d + kl)) : mk<T>(0, 0);
+        for (int p = 0; p < NB - 1; ++p) {
+          cx<T> up;
+          up.re = __shfl_sync(0xffffffffu, u.re, p);
+          up.im = __shfl_sync(0xffffffffu, u.im, p);
+          if (r > p) cfms(u, L11[r][p], up);
         }
-#pragma unroll
-        for (int r = 1; r < NB; ++r)
-#pragma unroll
-          for (int p = 0; p < r; ++p) cfms(u[r], L11[r][p], u[p]);
-#pragma unroll
-        for (int r = 0; r < NB; ++r) {
-          const int d = c - (k + r);
-          if (r < nb && d <= ku) Bd[(size_t)(k + r) * W + (d + kl)] = u[r];
-          Us[r][tid] = u[r];
-        }
+        if (in) Bd[(size_t)(k + r) * W + (d + kl)] = u;
+        Us[r][slot] = u;
       }
       __syncthreads();
       // A22 -= L21 U12: warp pair per 64 owned slots, 8 row chunks; lanes on
@@ -484,7 +494,26 @@ __global__ void __cluster_dims__(FCL, 1, 1) __launch_bounds__(FNT)
 // The FP64 factorisation is bound by the FP64 pipes; the per-step launches
 // spread its trailing updates over every SM, which measured faster there.
 template <typename T> bool band_factor_cluster_ok(int kl, int ku) {
-  return sizeof(T) == 4 && FactorCfg<T>::NB + kl <= FNT && ku <= (FMAXC / FGW) * FGW * FCL - 2 * FGW;
+  return sizeof(T) == 4 && FactorCfg<T>::NB + kl <= FNT && ku <= (FMAXC / FGW) * FGW * 8 - 2 * FGW;
+}
+
+// resident clusters of CL CTAs with the largest shared-memory request
+template <typename T, int CL>
+static int factor_cluster_capacity() {
+  auto kern = k_band_factor_cluster<T, FactorCfg<T>::NB, CL>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess ||
+      (CL > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL, 1, 1);
+  cfg.blockDim = dim3(FNT, 1, 1);
+  cfg.dynamicSmemBytes = 160 * 1024;
+  int nc = 0;
+  if (cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) != cudaSuccess) nc = 0;
+  cudaGetLastError();
+  return nc;
 }
 
 template <typename T> bool band_fits(int kl, int ku) {
@@ -498,22 +527,22 @@ template <typename T>
 cudaError_t band_factor(int n, int kl, int ku, int ne, cx<T> *band, int *d_err, cudaStream_t s) {
   constexpr int NB = FactorCfg<T>::NB;
   const size_t ns = (size_t)n * (kl + ku + 1);
-  static int cluster_fits = -1;  // can one FCL-CTA cluster be resident at all?
+  static int cap16 = -1, cap8 = -1;  // resident 16- and 8-CTA clusters
   const size_t fsmem = (size_t)kl * NB * sizeof(cx<T>);
-  if (cluster_fits < 0) {
-    cudaFuncSetAttribute(k_band_factor_cluster<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(FCL, 1, 1);
-    cfg.blockDim = dim3(FNT, 1, 1);
-    cfg.dynamicSmemBytes = 160 * 1024;
-    int nc = 0;
-    cluster_fits = (cudaOccupancyMaxActiveClusters(&nc, k_band_factor_cluster<T, NB>, &cfg) == cudaSuccess && nc > 0);
-    cudaGetLastError();
-  }
-  if (cluster_fits && band_factor_cluster_ok<T>(kl, ku) && fsmem <= 160 * 1024) {
-    k_band_factor_cluster<T, NB><<<dim3(FCL, ne), FNT, fsmem, s>>>(n, kl, ku, band, ns, d_err);
-    note_launch();
-    return cudaGetLastError();
+  if constexpr (sizeof(T) == 4) {
+    if (cap8 < 0) {
+      cap16 = factor_cluster_capacity<T, 16>();
+      cap8 = factor_cluster_capacity<T, 8>();
+    }
+    if (band_factor_cluster_ok<T>(kl, ku) && fsmem <= 160 * 1024 && (cap16 >= ne || cap8 > 0)) {
+      // 16-CTA clusters when every factor slot gets one at once, else 8
+      if (cap16 >= ne)
+        k_band_factor_cluster<T, NB, 16><<<dim3(16, ne), FNT, fsmem, s>>>(n, kl, ku, band, ns, d_err);
+      else
+        k_band_factor_cluster<T, NB, 8><<<dim3(8, ne), FNT, fsmem, s>>>(n, kl, ku, band, ns, d_err);
+      note_launch();
+      return cudaGetLastError();
+    }
   }
   const size_t smem = panel_smem<T>(kl, ku, NB);
   const bool reg = NB + kl <= 512;
