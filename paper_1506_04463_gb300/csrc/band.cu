@@ -176,6 +176,10 @@ __global__ void __launch_bounds__(256) k_band_panel(int n, int kl, int ku, int k
   }
 }
 
+template <typename T> __device__ __forceinline__ T rcp_rn(T x);
+template <> __device__ __forceinline__ float rcp_rn<float>(float x) { return __frcp_rn(x); }
+template <> __device__ __forceinline__ double rcp_rn<double>(double x) { return __drcp_rn(x); }
+
 // Register panel elimination with compile-time column indices: thread i holds
 // row i of the panel in row[]; prow_s is a double-buffered pivot row and
 // pinv_s the reciprocal of its pivot, formed once by the pivot thread.
@@ -195,8 +199,10 @@ __device__ __forceinline__ void panel_eliminate(cx<T> (&row)[NB], cx<T> (*prow_s
           atomicOr(err, DEVERR_ZERO_PIVOT);
           pinv_s[p & 1] = mk<T>(0, 0);
         } else {
-          const T ar = piv.re / sc, ai = piv.im / sc, den = (ar * ar + ai * ai) * sc;
-          pinv_s[p & 1] = mk<T>(ar / den, -ai / den);
+          // conj(piv) / |piv|^2 with the scale sc kept out of the squares
+          const T rs = rcp_rn(sc), ar = piv.re * rs, ai = piv.im * rs;
+          const T rd = rcp_rn(ar * ar + ai * ai) * rs;
+          pinv_s[p & 1] = mk<T>(ar * rd, -ai * rd);
         }
       }
       __syncthreads();
@@ -346,9 +352,8 @@ __global__ void __launch_bounds__(256) k_band_update(int n, int kl, int ku, int 
 // owned columns of a CTA to fit FMAXC.
 // ---------------------------------------------------------------------------
 constexpr int FNT = 512;     // threads per CTA
-constexpr int FGW = 16;      // column-group width
+constexpr int FGW = 8;       // column-group width
 constexpr int FMAXC = 64;    // columns a CTA owns per step
-constexpr int FRC = 64;      // rows of L21 staged per chunk
 
 template <typename T>
 __device__ __forceinline__ cx<T> ldcg(const cx<T> *p) {
@@ -368,13 +373,17 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(FNT)
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<T> *Ls = reinterpret_cast<cx<T> *>(smem_raw);  // kl x NB: L21 of the current step
+  // L21 of the current step (kl x NB); in the owner CTA, before that, the
+  // panel staged for coalesced loads and stores ((NB + kl) x (NB + 1))
+  cx<T> *Ls = reinterpret_cast<cx<T> *>(smem_raw);
+  cx<T> *Ps = Ls;
+  constexpr int PLD = NB + 1;
+  constexpr int UNR = 8;  // loads in flight per thread while staging
   __shared__ cx<T> prow_s[2][NB];
   __shared__ cx<T> pinv_s[2];
   __shared__ cx<T> L11[NB][NB + 1];
   __shared__ cx<T> Us[NB][FMAXC];
   __shared__ int mycol[FMAXC];
-  __shared__ int nmy_s;
   const int W = kl + ku + 1;
   cx<T> *Bd = band + (size_t)blockIdx.y * ns;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -384,21 +393,36 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(FNT)
     // ---------------- panel (owner CTA) ----------------
     if (rank == owner) {
       const int prow = min(n - k, nb + kl);
+      // coalesced staging: one row per warp and pass, lane = column
+      for (int i0 = warp; i0 < prow; i0 += UNR * (FNT / 32)) {
+        cx<T> v[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+          const int i = i0 + u * (FNT / 32), d = lane - i;
+          v[u] = (i < prow && lane < nb && d >= -kl && d <= ku) ? ldcg(Bd + (size_t)(k + i) * W + (d + kl))
+                                                              : mk<T>(0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+          const int i = i0 + u * (FNT / 32);
+          if (i < prow) Ps[i * PLD + lane] = v[u];
+        }
+      }
+      __syncthreads();
       const int i = tid;
       const bool own = i < prow;
       cx<T> row[NB];
 #pragma unroll
-      for (int q = 0; q < NB; ++q) {
-        const int d = q - i;
-        row[q] = (own && q < nb && d >= -kl && d <= ku) ? ldcg(Bd + (size_t)(k + i) * W + (d + kl)) : mk<T>(0, 0);
-      }
+      for (int q = 0; q < NB; ++q) row[q] = own ? Ps[i * PLD + q] : mk<T>(0, 0);
       panel_eliminate<T, NB>(row, prow_s, pinv_s, i, own, nb, kl, err);
       if (own) {
 #pragma unroll
-        for (int q = 0; q < NB; ++q) {
-          const int d = q - i;
-          if (q < nb && d >= -kl && d <= ku) Bd[(size_t)(k + i) * W + (d + kl)] = row[q];
-        }
+        for (int q = 0; q < NB; ++q) Ps[i * PLD + q] = row[q];
+      }
+      __syncthreads();
+      for (int i1 = warp; i1 < prow; i1 += FNT / 32) {
+        const int d = lane - i1;
+        if (lane < nb && d >= -kl && d <= ku) Bd[(size_t)(k + i1) * W + (d + kl)] = Ps[i1 * PLD + lane];
       }
     }
     cluster.sync();
@@ -406,56 +430,83 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(FNT)
     const int c_beg = k + nb, c_end = min(n, k + nb + ku), r_end = min(n, k + nb + kl);
     const int nrows = r_end - c_beg;
     if (c_beg < c_end && nrows > 0) {
-      // owned columns: slot t -> group g0 + 8*(t/16), column 16g + t%16 (or -1)
+      // owned columns: slot t -> group g0 + CL*(t/FGW), column FGW*g + t%FGW;
+      // in column order, so the valid slots are one run [t_lo, t_lo + nv)
+      int cslot = -1;
       if (tid < FMAXC) {
         int g0 = c_beg / FGW;
         g0 += ((rank - g0) % CL + CL) % CL;
-        const int c = (g0 + CL * (tid / FGW)) * FGW + tid % FGW;
-        mycol[tid] = (c >= c_beg && c < c_end) ? c : -1;
+        cslot = (g0 + CL * (tid / FGW)) * FGW + tid % FGW;
+        mycol[tid] = (cslot >= c_beg && cslot < c_end) ? cslot : -1;
       }
       for (int e = tid; e < NB * NB; e += FNT) {
         const int r = e / NB, p = e - r * NB;
         L11[r][p] = (r < nb && p < r && r - p <= kl) ? ldcg(Bd + (size_t)(k + r) * W + (p - r + kl)) : mk<T>(0, 0);
       }
-      for (int e = tid; e < nrows * NB; e += FNT) {
-        const int rr = e / NB, p = e - rr * NB;
-        const int r = c_beg + rr;
-        Ls[e] = (p < nb && r - (k + p) <= kl) ? ldcg(Bd + (size_t)r * W + (k + p - r + kl)) : mk<T>(0, 0);
+      const int tot = nrows * NB;
+      for (int e0 = tid; e0 < tot; e0 += UNR * FNT) {
+        cx<T> v[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+          const int e = e0 + u * FNT;
+          const int rr = e / NB, p = e - rr * NB;
+          const int r = c_beg + rr;
+          v[u] = (e < tot && p < nb && r - (k + p) <= kl) ? ldcg(Bd + (size_t)r * W + (k + p - r + kl)) : mk<T>(0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+          const int e = e0 + u * FNT;
+          if (e < tot) Ls[e] = v[u];
+        }
       }
-      __syncthreads();
-      // U12 = L11^{-1} A12, one warp per owned column, lane = row
+      const int nv = __syncthreads_count(tid < FMAXC && cslot >= c_beg && cslot < c_end);
+      const int t_lo = __syncthreads_count(tid < FMAXC && cslot < c_beg);
+      // U12 = L11^{-1} A12: each warp solves four owned columns side by side,
+      // lane = row, the solved entries passed on by shuffles
       static_assert(sizeof(T) != 4 || NB == 32, "one lane per panel row");
-      for (int slot = warp; slot < FMAXC; slot += FNT / 32) {
-        const int c = mycol[slot];
-        if (c < 0) continue;
+      static_assert(FMAXC == 4 * (FNT / 32), "four slots per warp");
+      {
         const int r = lane;
-        const int d = c - (k + r);
-        const bool in = r < nb && d <= ku;
-        cx<T> u = in ? ldcg(Bd + (size_t)(k + r) * W + (d + kl)) : mk<T>(0, 0);
+        cx<T> u[4];
+        bool in[4];
+        int cc[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          cc[a] = mycol[warp + a * (FNT / 32)];
+          const int d = cc[a] - (k + r);
+          in[a] = cc[a] >= 0 && r < nb && d <= ku;
+          u[a] = in[a] ? ldcg(Bd + (size_t)(k + r) * W + (d + kl)) : mk<T>(0, 0);
+        }
 #pragma unroll
         for (int p = 0; p < NB - 1; ++p) {
-          cx<T> up;
-          up.re = __shfl_sync(0xffffffffu, u.re, p);
-          up.im = __shfl_sync(0xffffffffu, u.im, p);
-          if (r > p) cfms(u, L11[r][p], up);
+          const cx<T> l = L11[r][p];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            cx<T> up;
+            up.re = __shfl_sync(0xffffffffu, u[a].re, p);
+            up.im = __shfl_sync(0xffffffffu, u[a].im, p);
+            if (r > p) cfms(u[a], l, up);
+          }
         }
-        if (in) Bd[(size_t)(k + r) * W + (d + kl)] = u;
-        Us[r][slot] = u;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          if (in[a]) Bd[(size_t)(k + r) * W + (cc[a] - (k + r) + kl)] = u[a];
+          Us[r][warp + a * (FNT / 32)] = u[a];
+        }
       }
       __syncthreads();
-      // A22 -= L21 U12: warp pair per 64 owned slots, 8 row chunks; lanes on
-      // consecutive owned columns (coalesced along band rows), U12 column in
-      // registers, L21 entries as shared-memory broadcasts, 4 rows at a time
-      // with the next 4 entries loaded ahead.
-      const int j = (warp & 1) * 32 + lane;
-      const int chunk = warp >> 1;
-      const int c = mycol[j];
-      if (c >= 0) {
+      // A22 -= L21 U12: threads on (owned column, row chunk) pairs, consecutive
+      // threads on consecutive columns (coalesced along band rows), U12 column
+      // in registers, L21 entry pairs as shared-memory broadcasts, 4 rows at a
+      // time with the next 4 entries loaded ahead.
+      const int nch = nv > 0 ? FNT / nv : 0;
+      if (nv > 0 && tid < nch * nv) {
+        const int slot = t_lo + tid % nv, chunk = tid / nv;
+        const int c = mycol[slot];
         cx<T> u[NB];
 #pragma unroll
-        for (int p = 0; p < NB; ++p) u[p] = Us[p][j];
-        constexpr int NCH = FNT / 64;
-        const int per = ((nrows + NCH - 1) / NCH + 3) & ~3;
+        for (int p = 0; p < NB; ++p) u[p] = Us[p][slot];
+        const int per = ((nrows + nch - 1) / nch + 3) & ~3;
         const int rb = chunk * per, re = min(nrows, rb + per);
         cx<T> cur[4], nxt[4];
 #pragma unroll
@@ -472,11 +523,21 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(FNT)
             nxt[q] = rr < re ? ldcg(Bd + (size_t)(c_beg + rr) * W + (c - (c_beg + rr) + kl)) : mk<T>(0, 0);
           }
 #pragma unroll
-          for (int p = 0; p < NB; ++p) {
+          for (int q = 0; q < 4; ++q) {
+            const cx<T> *lrow = Ls + (size_t)min(r4 + q, nrows - 1) * NB;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const int rr = min(r4 + q, nrows - 1);
-              cfms(cur[q], Ls[rr * NB + p], u[p]);
+            for (int p = 0; p < NB; p += 2) {
+              cx<T> l0, l1;
+              if constexpr (sizeof(T) == 4) {
+                const float4 l2 = *reinterpret_cast<const float4 *>(lrow + p);
+                l0 = mk<T>(l2.x, l2.y);
+                l1 = mk<T>(l2.z, l2.w);
+              } else {
+                l0 = lrow[p];
+                l1 = lrow[p + 1];
+              }
+              cfms(cur[q], l0, u[p]);
+              cfms(cur[q], l1, u[p + 1]);
             }
           }
 #pragma unroll
@@ -528,7 +589,7 @@ cudaError_t band_factor(int n, int kl, int ku, int ne, cx<T> *band, int *d_err, 
   constexpr int NB = FactorCfg<T>::NB;
   const size_t ns = (size_t)n * (kl + ku + 1);
   static int cap16 = -1, cap8 = -1;  // resident 16- and 8-CTA clusters
-  const size_t fsmem = (size_t)kl * NB * sizeof(cx<T>);
+  const size_t fsmem = (size_t)(NB + kl) * (NB + 1) * sizeof(cx<T>);  // >= kl x NB of L21
   if constexpr (sizeof(T) == 4) {
     if (cap8 < 0) {
       cap16 = factor_cluster_capacity<T, 16>();
