@@ -342,17 +342,17 @@ __global__ void __launch_bounds__(256) k_band_update(int n, int kl, int ku, int 
 
 // ---------------------------------------------------------------------------
 // factorisation as one persistent launch: one thread-block cluster of CL CTAs
-// per node.  Step k (columns [k, k+nb)): the CTA owning the panel factors it
-// in registers (thread = row); cluster barrier; every CTA forms U12 for the
-// 16-column groups it owns (group g belongs to CTA g mod CL; one warp per
-// column, lane = row, the solved entries passed on by shuffles) and applies
-// the rank-nb update to its columns of the trailing window; cluster barrier.
+// per node.  Panels of NB columns are factored in registers (thread = row) by
+// CTA (panel index mod CL).  During step k the other CL - 1 CTAs split the
+// trailing window of panel k by columns, form U12 for their columns (one warp
+// per column, lane = row, the solved entries passed on by shuffles) and apply
+// the rank-nb update, the next panel's columns first; as soon as those are
+// done the next panel's owner factors it, overlapping the rest of the update.
 // Band data shared between CTAs is read with ld.global.cg (L2), so no CTA can
-// see a stale L1 line.  Requires nb + kl <= 512 and ku small enough for the
-// owned columns of a CTA to fit FMAXC.
+// see a stale L1 line; cluster barriers (release / acquire) order the steps.
+// Requires nb + kl <= 512 and a worker's share of the window <= FMAXC columns.
 // ---------------------------------------------------------------------------
 constexpr int FNT = 512;     // threads per CTA
-constexpr int FGW = 8;       // column-group width
 constexpr int FMAXC = 64;    // columns a CTA owns per step
 
 template <typename T>
@@ -366,6 +366,13 @@ __device__ __forceinline__ cx<T> ldcg(const cx<T> *p) {
   }
 }
 
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory"); }
+
+// Step k (panel columns [k, k+nb) already factored): the CTA that owns the
+// next panel waits only until the other CL-1 CTAs have applied step k's
+// update to that panel's columns (first cluster-barrier phase), then factors
+// it, while the others update the rest of the trailing window (look-ahead).
 template <typename T, int NB, int CL>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(FNT)
     k_band_factor_cluster(int n, int kl, int ku, cx<T> *band, size_t ns, int *err) {
@@ -373,8 +380,8 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(FNT)
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // L21 of the current step (kl x NB); in the owner CTA, before that, the
-  // panel staged for coalesced loads and stores ((NB + kl) x (NB + 1))
+  // L21 of the current step (kl x NB) in the updating CTAs; the next panel
+  // staged for coalesced loads and stores ((NB + kl) x (NB + 1)) in its owner
   cx<T> *Ls = reinterpret_cast<cx<T> *>(smem_raw);
   cx<T> *Ps = Ls;
   constexpr int PLD = NB + 1;
@@ -383,179 +390,199 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(FNT)
   __shared__ cx<T> pinv_s[2];
   __shared__ cx<T> L11[NB][NB + 1];
   __shared__ cx<T> Us[NB][FMAXC];
-  __shared__ int mycol[FMAXC];
   const int W = kl + ku + 1;
   cx<T> *Bd = band + (size_t)blockIdx.y * ns;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int k = 0; k < n; k += NB) {
+
+  // factor the panel at columns [k, k+nb) in registers (thread = row)
+  auto factor_panel = [&](int k) {
     const int nb = min(NB, n - k);
-    const int owner = (k / NB) % CL;
-    // ---------------- panel (owner CTA) ----------------
-    if (rank == owner) {
-      const int prow = min(n - k, nb + kl);
-      // coalesced staging: one row per warp and pass, lane = column
-      for (int i0 = warp; i0 < prow; i0 += UNR * (FNT / 32)) {
-        cx<T> v[UNR];
+    const int prow = min(n - k, nb + kl);
+    for (int i0 = warp; i0 < prow; i0 += UNR * (FNT / 32)) {
+      cx<T> v[UNR];
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) {
-          const int i = i0 + u * (FNT / 32), d = lane - i;
-          v[u] = (i < prow && lane < nb && d >= -kl && d <= ku) ? ldcg(Bd + (size_t)(k + i) * W + (d + kl))
-                                                              : mk<T>(0, 0);
-        }
-#pragma unroll
-        for (int u = 0; u < UNR; ++u) {
-          const int i = i0 + u * (FNT / 32);
-          if (i < prow) Ps[i * PLD + lane] = v[u];
-        }
+      for (int u = 0; u < UNR; ++u) {
+        const int i = i0 + u * (FNT / 32), d = lane - i;
+        v[u] = (i < prow && lane < nb && d >= -kl && d <= ku) ? ldcg(Bd + (size_t)(k + i) * W + (d + kl))
+                                                            : mk<T>(0, 0);
       }
-      __syncthreads();
-      const int i = tid;
-      const bool own = i < prow;
-      cx<T> row[NB];
 #pragma unroll
-      for (int q = 0; q < NB; ++q) row[q] = own ? Ps[i * PLD + q] : mk<T>(0, 0);
-      panel_eliminate<T, NB>(row, prow_s, pinv_s, i, own, nb, kl, err);
-      if (own) {
-#pragma unroll
-        for (int q = 0; q < NB; ++q) Ps[i * PLD + q] = row[q];
-      }
-      __syncthreads();
-      for (int i1 = warp; i1 < prow; i1 += FNT / 32) {
-        const int d = lane - i1;
-        if (lane < nb && d >= -kl && d <= ku) Bd[(size_t)(k + i1) * W + (d + kl)] = Ps[i1 * PLD + lane];
+      for (int u = 0; u < UNR; ++u) {
+        const int i = i0 + u * (FNT / 32);
+        if (i < prow) Ps[i * PLD + lane] = v[u];
       }
     }
-    cluster.sync();
-    // ---------------- U12 and trailing update (all CTAs) ----------------
-    const int c_beg = k + nb, c_end = min(n, k + nb + ku), r_end = min(n, k + nb + kl);
+    __syncthreads();
+    const int i = tid;
+    const bool own = i < prow;
+    cx<T> row[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) row[q] = own ? Ps[i * PLD + q] : mk<T>(0, 0);
+    panel_eliminate<T, NB>(row, prow_s, pinv_s, i, own, nb, kl, err);
+    if (own) {
+#pragma unroll
+      for (int q = 0; q < NB; ++q) Ps[i * PLD + q] = row[q];
+    }
+    __syncthreads();
+    for (int i1 = warp; i1 < prow; i1 += FNT / 32) {
+      const int d = lane - i1;
+      if (lane < nb && d >= -kl && d <= ku) Bd[(size_t)(k + i1) * W + (d + kl)] = Ps[i1 * PLD + lane];
+    }
+  };
+
+  // U12 = L11^{-1} A12 and A22 -= L21 U12 for columns [a, b) (b - a <= FMAXC)
+  // of the trailing window of the panel at k; L11, L21 staged
+  auto update_cols = [&](int k, int a, int b) {
+    const int nb = min(NB, n - k);
+    const int c_beg = k + nb, r_end = min(n, k + nb + kl);
     const int nrows = r_end - c_beg;
-    if (c_beg < c_end && nrows > 0) {
-      // owned columns: slot t -> group g0 + CL*(t/FGW), column FGW*g + t%FGW;
-      // in column order, so the valid slots are one run [t_lo, t_lo + nv)
-      int cslot = -1;
-      if (tid < FMAXC) {
-        int g0 = c_beg / FGW;
-        g0 += ((rank - g0) % CL + CL) % CL;
-        cslot = (g0 + CL * (tid / FGW)) * FGW + tid % FGW;
-        mycol[tid] = (cslot >= c_beg && cslot < c_end) ? cslot : -1;
-      }
-      for (int e = tid; e < NB * NB; e += FNT) {
-        const int r = e / NB, p = e - r * NB;
-        L11[r][p] = (r < nb && p < r && r - p <= kl) ? ldcg(Bd + (size_t)(k + r) * W + (p - r + kl)) : mk<T>(0, 0);
-      }
-      const int tot = nrows * NB;
-      for (int e0 = tid; e0 < tot; e0 += UNR * FNT) {
-        cx<T> v[UNR];
+    const int ncol = b - a;
+    if (ncol <= 0) return;
+    // U12: each warp solves four columns side by side, lane = row, the solved
+    // entries passed on by shuffles
+    {
+      const int r = lane;
+      cx<T> u[4];
+      bool in[4];
+      int cc[4];
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) {
-          const int e = e0 + u * FNT;
-          const int rr = e / NB, p = e - rr * NB;
-          const int r = c_beg + rr;
-          v[u] = (e < tot && p < nb && r - (k + p) <= kl) ? ldcg(Bd + (size_t)r * W + (k + p - r + kl)) : mk<T>(0, 0);
-        }
+      for (int s = 0; s < 4; ++s) {
+        const int slot = warp + s * (FNT / 32);
+        cc[s] = slot < ncol ? a + slot : -1;
+        const int d = cc[s] - (k + r);
+        in[s] = cc[s] >= 0 && r < nb && d <= ku;
+        u[s] = in[s] ? ldcg(Bd + (size_t)(k + r) * W + (d + kl)) : mk<T>(0, 0);
+      }
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) {
-          const int e = e0 + u * FNT;
-          if (e < tot) Ls[e] = v[u];
+      for (int p = 0; p < NB - 1; ++p) {
+        const cx<T> l = L11[r][p];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          cx<T> up;
+          up.re = __shfl_sync(0xffffffffu, u[s].re, p);
+          up.im = __shfl_sync(0xffffffffu, u[s].im, p);
+          if (r > p) cfms(u[s], l, up);
         }
       }
-      const int nv = __syncthreads_count(tid < FMAXC && cslot >= c_beg && cslot < c_end);
-      const int t_lo = __syncthreads_count(tid < FMAXC && cslot < c_beg);
-      // U12 = L11^{-1} A12: each warp solves four owned columns side by side,
-      // lane = row, the solved entries passed on by shuffles
-      static_assert(sizeof(T) != 4 || NB == 32, "one lane per panel row");
-      static_assert(FMAXC == 4 * (FNT / 32), "four slots per warp");
-      {
-        const int r = lane;
-        cx<T> u[4];
-        bool in[4];
-        int cc[4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          cc[a] = mycol[warp + a * (FNT / 32)];
-          const int d = cc[a] - (k + r);
-          in[a] = cc[a] >= 0 && r < nb && d <= ku;
-          u[a] = in[a] ? ldcg(Bd + (size_t)(k + r) * W + (d + kl)) : mk<T>(0, 0);
-        }
-#pragma unroll
-        for (int p = 0; p < NB - 1; ++p) {
-          const cx<T> l = L11[r][p];
-#pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            cx<T> up;
-            up.re = __shfl_sync(0xffffffffu, u[a].re, p);
-            up.im = __shfl_sync(0xffffffffu, u[a].im, p);
-            if (r > p) cfms(u[a], l, up);
-          }
-        }
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          if (in[a]) Bd[(size_t)(k + r) * W + (cc[a] - (k + r) + kl)] = u[a];
-          Us[r][warp + a * (FNT / 32)] = u[a];
-        }
+      for (int s = 0; s < 4; ++s) {
+        if (in[s]) Bd[(size_t)(k + r) * W + (cc[s] - (k + r) + kl)] = u[s];
+        Us[r][warp + s * (FNT / 32)] = u[s];
       }
-      __syncthreads();
-      // A22 -= L21 U12: threads on (owned column, row chunk) pairs, consecutive
-      // threads on consecutive columns (coalesced along band rows), U12 column
-      // in registers, L21 entry pairs as shared-memory broadcasts, 4 rows at a
-      // time with the next 4 entries loaded ahead.
-      const int nch = nv > 0 ? FNT / nv : 0;
-      if (nv > 0 && tid < nch * nv) {
-        const int slot = t_lo + tid % nv, chunk = tid / nv;
-        const int c = mycol[slot];
-        cx<T> u[NB];
+    }
+    __syncthreads();
+    // update: threads on (column, row chunk) pairs, consecutive threads on
+    // consecutive columns (coalesced along band rows), U12 column in
+    // registers, L21 entry pairs as shared-memory broadcasts, 4 rows at a
+    // time with the next 4 entries loaded ahead
+    const int nch = FNT / ncol;
+    if (tid < nch * ncol) {
+      const int slot = tid % ncol, chunk = tid / ncol;
+      const int c = a + slot;
+      cx<T> u[NB];
 #pragma unroll
-        for (int p = 0; p < NB; ++p) u[p] = Us[p][slot];
-        const int per = ((nrows + nch - 1) / nch + 3) & ~3;
-        const int rb = chunk * per, re = min(nrows, rb + per);
-        cx<T> cur[4], nxt[4];
+      for (int p = 0; p < NB; ++p) u[p] = Us[p][slot];
+      const int per = ((nrows + nch - 1) / nch + 3) & ~3;
+      const int rb = chunk * per, re = min(nrows, rb + per);
+      cx<T> cur[4], nxt[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int rr = rb + q;
+        nxt[q] = rr < re ? ldcg(Bd + (size_t)(c_beg + rr) * W + (c - (c_beg + rr) + kl)) : mk<T>(0, 0);
+      }
+      for (int r4 = rb; r4 < re; r4 += 4) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cur[q] = nxt[q];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const int rr = rb + q;
+          const int rr = r4 + 4 + q;
           nxt[q] = rr < re ? ldcg(Bd + (size_t)(c_beg + rr) * W + (c - (c_beg + rr) + kl)) : mk<T>(0, 0);
         }
-        for (int r4 = rb; r4 < re; r4 += 4) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) cur[q] = nxt[q];
+        for (int q = 0; q < 4; ++q) {
+          const cx<T> *lrow = Ls + (size_t)min(r4 + q, nrows - 1) * NB;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int rr = r4 + 4 + q;
-            nxt[q] = rr < re ? ldcg(Bd + (size_t)(c_beg + rr) * W + (c - (c_beg + rr) + kl)) : mk<T>(0, 0);
-          }
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const cx<T> *lrow = Ls + (size_t)min(r4 + q, nrows - 1) * NB;
-#pragma unroll
-            for (int p = 0; p < NB; p += 2) {
-              cx<T> l0, l1;
-              if constexpr (sizeof(T) == 4) {
-                const float4 l2 = *reinterpret_cast<const float4 *>(lrow + p);
-                l0 = mk<T>(l2.x, l2.y);
-                l1 = mk<T>(l2.z, l2.w);
-              } else {
-                l0 = lrow[p];
-                l1 = lrow[p + 1];
-              }
-              cfms(cur[q], l0, u[p]);
-              cfms(cur[q], l1, u[p + 1]);
+          for (int p = 0; p < NB; p += 2) {
+            cx<T> l0, l1;
+            if constexpr (sizeof(T) == 4) {
+              const float4 l2 = *reinterpret_cast<const float4 *>(lrow + p);
+              l0 = mk<T>(l2.x, l2.y);
+              l1 = mk<T>(l2.z, l2.w);
+            } else {
+              l0 = lrow[p];
+              l1 = lrow[p + 1];
             }
+            cfms(cur[q], l0, u[p]);
+            cfms(cur[q], l1, u[p + 1]);
           }
+        }
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int rr = r4 + q;
-            if (rr < re) Bd[(size_t)(c_beg + rr) * W + (c - (c_beg + rr) + kl)] = cur[q];
-          }
+        for (int q = 0; q < 4; ++q) {
+          const int rr = r4 + q;
+          if (rr < re) Bd[(size_t)(c_beg + rr) * W + (c - (c_beg + rr) + kl)] = cur[q];
         }
       }
     }
-    cluster.sync();
+    __syncthreads();
+  };
+
+  if (rank == 0) factor_panel(0);
+  cluster_arrive();
+  cluster_wait();
+  for (int k = 0; k < n; k += NB) {
+    const int nb = min(NB, n - k);
+    const int next_owner = (k / NB + 1) % CL;
+    const int c_beg = k + nb, c_end = min(n, k + nb + ku), r_end = min(n, k + nb + kl);
+    const int nrows = r_end - c_beg;
+    if (rank != next_owner) {
+      const int w = (rank - next_owner - 1 + CL) % CL;  // worker index in [0, CL-1)
+      const bool work = c_beg < c_end && nrows > 0;
+      if (work) {
+        for (int e = tid; e < NB * NB; e += FNT) {
+          const int r = e / NB, p = e - r * NB;
+          L11[r][p] = (r < nb && p < r && r - p <= kl) ? ldcg(Bd + (size_t)(k + r) * W + (p - r + kl)) : mk<T>(0, 0);
+        }
+        const int tot = nrows * NB;
+        for (int e0 = tid; e0 < tot; e0 += UNR * FNT) {
+          cx<T> v[UNR];
+#pragma unroll
+          for (int u = 0; u < UNR; ++u) {
+            const int e = e0 + u * FNT;
+            const int rr = e / NB, p = e - rr * NB;
+            const int r = c_beg + rr;
+            v[u] = (e < tot && p < nb && r - (k + p) <= kl) ? ldcg(Bd + (size_t)r * W + (k + p - r + kl))
+                                                            : mk<T>(0, 0);
+          }
+#pragma unroll
+          for (int u = 0; u < UNR; ++u) {
+            const int e = e0 + u * FNT;
+            if (e < tot) Ls[e] = v[u];
+          }
+        }
+        __syncthreads();
+      }
+      // the next panel's columns first, then the rest, each split evenly
+      const int pe = min(c_end, c_beg + NB);
+      if (work) update_cols(k, c_beg + (pe - c_beg) * w / (CL - 1), c_beg + (pe - c_beg) * (w + 1) / (CL - 1));
+      cluster_arrive();
+      if (work) update_cols(k, pe + (c_end - pe) * w / (CL - 1), pe + (c_end - pe) * (w + 1) / (CL - 1));
+      cluster_wait();
+    } else {
+      cluster_arrive();
+      cluster_wait();
+      if (k + NB < n) factor_panel(k + NB);
+    }
+    cluster_arrive();
+    cluster_wait();
   }
 }
 
 // The FP64 factorisation is bound by the FP64 pipes; the per-step launches
 // spread its trailing updates over every SM, which measured faster there.
+// the panel rows fit one thread each, and a worker's share of the trailing
+// window (CL - 1 = 7 workers at least) fits FMAXC columns
 template <typename T> bool band_factor_cluster_ok(int kl, int ku) {
-  return sizeof(T) == 4 && FactorCfg<T>::NB + kl <= FNT && ku <= (FMAXC / FGW) * FGW * 8 - 2 * FGW;
+  return sizeof(T) == 4 && FactorCfg<T>::NB + kl <= FNT && ku + FactorCfg<T>::NB <= FMAXC * 7;
 }
 
 // resident clusters of CL CTAs with the largest shared-memory request
