@@ -338,7 +338,7 @@ __device__ __forceinline__ void givens(cxd a, cxd b, double &c, cxd &s) {
   s = (ra * rr) * (as * conj(bs));
 }
 
-__global__ void __launch_bounds__(256) k_small_eig(const cxd *A, int m, cxd *lam, cxd *V, cxd *work, int *err,
+__global__ void __launch_bounds__(256, 1) k_small_eig(const cxd *A, int m, cxd *lam, cxd *V, cxd *work, int *err,
                                                    int hsm) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ cxd v[kMaxM0];
@@ -347,6 +347,7 @@ __global__ void __launch_bounds__(256) k_small_eig(const cxd *A, int m, cxd *lam
   __shared__ double gcs[kMaxM0];
   __shared__ int sh_l, sh_hi, sh_done;
   __shared__ cxd sh_mu;
+  __shared__ double dsc[kMaxM0];  // balancing: H = D^{-1} A D, D = diag(dsc)
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
   const int ld = hsm ? (m | 1) : m;
   cxd *H = hsm ? reinterpret_cast<cxd *>(dsm) : work;
@@ -356,6 +357,55 @@ __global__ void __launch_bounds__(256) k_small_eig(const cxd *A, int m, cxd *lam
     const int i = e / m, j = e - i * m;
     H[(size_t)i * ld + j] = A[e];
     Z[e] = mk(i == j ? 1.0 : 0.0, 0.0);
+  }
+  for (int i = tid; i < m; i += nt) dsc[i] = 1.0;
+  __syncthreads();
+  // ---- balancing (Parlett-Reinsch, powers of two, one warp): for each i
+  // scale column i by f and row i by 1/f so that their off-diagonal 1-norms
+  // (|re| + |im|) come within a factor 2 of each other, until a whole pass
+  // changes nothing.  Exact in floating point; it keeps the entries of a
+  // reduced matrix whose rows and columns differ in scale by orders of
+  // magnitude comparable, so the local deflation test below is meaningful.
+  if (tid < 32) {
+    for (int pass = 0; pass < 64; ++pass) {
+      bool changed = false;
+      for (int i = 0; i < m; ++i) {
+        double c = 0.0, r = 0.0;
+        for (int j = lane; j < m; j += 32)
+          if (j != i) {
+            c += cabs1(H[(size_t)j * ld + i]);
+            r += cabs1(H[(size_t)i * ld + j]);
+          }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+          c += __shfl_xor_sync(0xffffffffu, c, o);
+          r += __shfl_xor_sync(0xffffffffu, r, o);
+        }
+        if (c == 0.0 || r == 0.0) continue;
+        const double s = c + r;
+        double f = 1.0;
+        for (int q = 0; q < 64 && c < 0.5 * r; ++q) {
+          c *= 2.0;
+          r *= 0.5;
+          f *= 2.0;
+        }
+        for (int q = 0; q < 64 && c >= 2.0 * r; ++q) {
+          c *= 0.5;
+          r *= 2.0;
+          f *= 0.5;
+        }
+        if (c + r >= 0.95 * s) continue;
+        changed = true;
+        const double fi = 1.0 / f;  // exact: f is a power of two
+        for (int j = lane; j < m; j += 32) {
+          H[(size_t)j * ld + i] = f * H[(size_t)j * ld + i];
+          H[(size_t)i * ld + j] = fi * H[(size_t)i * ld + j];
+        }
+        if (lane == 0) dsc[i] *= f;
+        __syncwarp();
+      }
+      if (!changed) break;
+    }
   }
   __syncthreads();
   // ---- Householder reduction to upper Hessenberg form: H = Z^H A Z ----
@@ -413,6 +463,26 @@ __global__ void __launch_bounds__(256) k_small_eig(const cxd *A, int m, cxd *lam
     __syncthreads();
   }
   // ---- shifted QR iteration to upper triangular (Schur) form ----
+  // A subdiagonal entry is negligible when it is below eps times its two
+  // diagonal neighbours, or, once 20 sweeps have not deflated the current
+  // eigenvalue, below m * eps * max|h_ij| (the size of the rounding errors of
+  // a sweep): without that fallback a graded matrix whose small eigenvalues
+  // sit at the rounding level never deflates.
+  {
+    double hmax = 0.0;
+    for (int e = tid; e < m * m; e += nt) {
+      const int i = e / m, j = e - i * m;
+      if (j + 1 >= i) hmax = fmax(hmax, cabs1(H[(size_t)i * ld + j]));
+    }
+    red[tid] = hmax;
+    __syncthreads();
+    for (int o = nt / 2; o; o >>= 1) {
+      if (tid < o) red[tid] = fmax(red[tid], red[tid + o]);
+      __syncthreads();
+    }
+  }
+  const double hfloor = (double)m * DBL_EPSILON * red[0];
+  __syncthreads();
   if (tid == 0) {
     sh_hi = m - 1;
     sh_done = 0;
@@ -427,7 +497,7 @@ __global__ void __launch_bounds__(256) k_small_eig(const cxd *A, int m, cxd *lam
       while (l > 0) {
         const double s = cabs1(H[(size_t)(l - 1) * ld + l - 1]) + cabs1(H[(size_t)l * ld + l]);
         const double sub = cabs1(H[(size_t)l * ld + l - 1]);
-        if (sub <= DBL_EPSILON * s || sub < 1e-300) break;
+        if (sub <= DBL_EPSILON * s || (its >= 20 && sub <= hfloor) || sub < 1e-300) break;
         --l;
       }
       if (l > 0) H[(size_t)l * ld + l - 1] = mk(0.0, 0.0);
@@ -550,7 +620,7 @@ __global__ void __launch_bounds__(256) k_small_eig(const cxd *A, int m, cxd *lam
     const int i = e / m, k = e - i * m;
     cxd s = mk(0.0, 0.0);
     for (int l2 = 0; l2 <= k; ++l2) cfma(s, Z[(size_t)i * m + l2], E[(size_t)l2 * m + k]);
-    V[e] = s;
+    V[e] = dsc[i] * s;  // eigenvectors of A = D (eigenvectors of H)
   }
   __syncthreads();
   for (int k = tid; k < m; k += nt) {
