@@ -313,9 +313,9 @@ __device__ void block_reduce_sum2(double &a, double *red) {
 // work layout: H (m*m; used when H does not fit in shared memory), Z (m*m), E (m*m).
 // H lives in dynamic shared memory (odd row stride) when it fits.  The QR
 // sweeps are explicit single-shift steps: the left rotations are formed and
-// applied by one warp, each lane owning the columns j = lane (mod 32), so a
-// rotation needs no block barrier; the right rotations of the whole sweep are
-// then applied row by row (rows are independent) to H and to Z.
+// applied by four warps, each thread owning one column, with one 128-thread
+// barrier per rotation; the right rotations of the whole sweep are then
+// applied row by row (rows are independent) to H and to Z.
 __device__ __forceinline__ void givens(cxd a, cxd b, double &c, cxd &s) {
   // (c, s) with c real, c^2 + |s|^2 = 1 and [c s; -conj(s) c] [a; b] = [r; 0]
   const double sc = fmax(fmax(fabs(a.re), fabs(a.im)), fmax(fabs(b.re), fabs(b.im)));
@@ -538,21 +538,25 @@ __global__ void __launch_bounds__(256, 1) k_small_eig(const cxd *A, int m, cxd *
     const cxd mu = sh_mu;
     for (int i = l + tid; i <= hi; i += nt) H[(size_t)i * ld + i] = H[(size_t)i * ld + i] - mu;
     __syncthreads();
-    // left rotations: warp 0, lane = owner of columns j = lane (mod 32)
-    if (tid < 32) {
+    // left rotations: warps 0-3, one per SM sub-partition (each sub-partition's
+    // FP64 pipe serves one warp at a time), thread 32w + lane owning column
+    // j = 4 lane + w; the owner of column k forms rotation k from its own
+    // column and publishes it through shared memory, one 128-thread named
+    // barrier per rotation
+    if (tid < 128) {
+      const int j = 4 * lane + (tid >> 5);
       for (int k = l; k < hi; ++k) {
-        const int ok = k & 31;
-        double c = 1.0;
-        cxd s = mk(0.0, 0.0);
-        if (lane == ok) {
+        if (j == k) {
+          double c;
+          cxd s;
           givens(H[(size_t)k * ld + k], H[(size_t)(k + 1) * ld + k], c, s);
           gcs[k] = c;
           gs[k] = s;
         }
-        c = __shfl_sync(0xffffffffu, c, ok);
-        s.re = __shfl_sync(0xffffffffu, s.re, ok);
-        s.im = __shfl_sync(0xffffffffu, s.im, ok);
-        for (int j = k + ((lane - k) & 31); j < m; j += 32) {
+        asm volatile("bar.sync 1, 128;\n" ::: "memory");
+        if (j >= k && j < m) {
+          const double c = gcs[k];
+          const cxd s = gs[k];
           cxd *p1 = H + (size_t)k * ld + j, *p2 = p1 + ld;
           const cxd h1 = *p1, h2 = *p2;
           *p1 = c * h1 + s * h2;
