@@ -1336,7 +1336,6 @@ __device__ __forceinline__ void kt_body(int n, int klp, int kup, int BX, const C
     long long spins = 0;
     while (!mbar_try_wait(&mbar[j & 1], (uint32_t)((j >> 1) & 1))) {
       if (++spins > kSpinLimit) return false;
-      if (spins > 32) __nanosleep(64);
     }
     return true;
   };
@@ -1421,7 +1420,7 @@ __device__ __forceinline__ void kt_body(int n, int klp, int kup, int BX, const C
         const cxf *p0 = Ms + rl * BX + (a + tbase - rl) + off;
         const cxf *p1 = Ms + (rl + 8) * BX + (a + tbase - rl - 8) + off;
         const int cnt = b - a;
-#pragma unroll 4
+#pragma unroll 8
         for (int k = 0; k < cnt; ++k) {
           const cxf mv0 = p0[k], mv1 = p1[k];
           const float4 ya = *reinterpret_cast<const float4 *>(py + k * R);
