@@ -193,7 +193,7 @@ def run_ours(args, rank, world, local_rank):
     # DRAM bytes (read + write) per k_band_solve_tma launch at N = 300, the mean
     # of the 6 launches of one solve in the ncu capture summarised in
     # profiles/k_band_solve_tma_convdiff2d.md; None for other sizes or forms
-    solve_traffic = 27.93e9 if (n == 90000 and prec == F.PREC_FP32_IR) else None
+    solve_traffic = 24.95e9 if (n == 90000 and prec == F.PREC_FP32_IR) else None
     roof = None
     if n_solve:
         avg = solve_ms / n_solve
