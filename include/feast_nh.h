@@ -89,7 +89,7 @@ typedef struct {
   double eps;         /* 1e-10  */
   double eta;         /* 1e-16  */
   double mu;          /* 0.1    */
-  double inner_tol;   /* 1e-11  */
+  double inner_tol;   /* 1e-10  */
   int32_t max_iter;   /* 100    */
   int32_t inner_max;  /* 12     */
   int32_t inner_kind; /* FEAST_NH_INNER_BANDED */

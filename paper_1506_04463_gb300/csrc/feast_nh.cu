@@ -447,7 +447,7 @@ void feast_nh_default_opts(feast_nh_opts *o) {
   o->eps = 1e-10;
   o->eta = 1e-16;
   o->mu = 0.1;
-  o->inner_tol = 1e-11;
+  o->inner_tol = 1e-10;
   o->max_iter = 100;
   o->inner_max = 12;
   o->inner_kind = FEAST_NH_INNER_BANDED;

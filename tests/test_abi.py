@@ -37,7 +37,7 @@ def test_exports_every_declared_symbol(L):
 
 def test_default_opts_and_strerror(L):
     o = F.default_opts()
-    assert (o.eps, o.eta, o.mu, o.inner_tol, o.max_iter) == (1e-10, 1e-16, 0.1, 1e-11, 100)
+    assert (o.eps, o.eta, o.mu, o.inner_tol, o.max_iter) == (1e-10, 1e-16, 0.1, 1e-10, 100)
     for s in range(8):
         assert len(L.feast_nh_strerror(s)) > 3
 
