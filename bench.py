@@ -191,9 +191,9 @@ def run_ours(args, rank, world, local_rank):
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12       # TFLOP/s at the max SM clock
     fp64_peak = 1.25                                          # nominal FP64 TFLOP/s of the part
     # DRAM bytes (read + write) per k_band_solve_tma launch at N = 300, the mean
-    # of the 6 launches of one solve in the ncu capture summarised in
+    # of the 5 launches of one solve in the ncu capture summarised in
     # profiles/k_band_solve_tma_convdiff2d.md; None for other sizes or forms
-    solve_traffic = 24.95e9 if (n == 90000 and prec == F.PREC_FP32_IR) else None
+    solve_traffic = 23.99e9 if (n == 90000 and prec == F.PREC_FP32_IR) else None
     roof = None
     if n_solve:
         avg = solve_ms / n_solve
