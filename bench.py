@@ -55,6 +55,19 @@ def rank_info():
     return r, w, lr
 
 
+def combine_ranks(total_ms, pairs, world, device):
+    """Whole-job figures of a replicas run: the slowest rank's timed total and
+    the converged pairs of all ranks (every rank solves its own problem)."""
+    import torch
+    t = torch.tensor([float(total_ms), float(pairs)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        tt = [torch.zeros_like(t) for _ in range(world)]
+        dist.all_gather(tt, t)
+        return max(float(x[0]) for x in tt), sum(float(x[1]) for x in tt)
+    return float(total_ms), float(pairs)
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -165,14 +178,7 @@ def run_ours(args, rank, world, local_rank):
     eig_err = float(np.max(np.abs(lam - exact) / np.abs(exact))) if lam.size == exact.size else None
     max_res = float(out["res"].max().item()) if out["m"] else None
     pairs = sum(ms_found)
-    t = torch.tensor([total_ms, float(pairs)], dtype=torch.float64, device=dev)
-    if world > 1:
-        tt = [torch.zeros_like(t) for _ in range(world)]
-        dist.all_gather(tt, t)
-        total_max = max(float(x[0]) for x in tt)
-        pairs_all = sum(float(x[1]) for x in tt)
-    else:
-        total_max, pairs_all = total_ms, float(pairs)
+    total_max, pairs_all = combine_ranks(total_ms, pairs, world, dev)
     value = pairs_all / (total_max / 1e3)
 
     # ---- dominant kernel and its roofline ----
