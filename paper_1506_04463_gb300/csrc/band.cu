@@ -615,17 +615,19 @@ template <typename T>
 cudaError_t band_factor(int n, int kl, int ku, int ne, cx<T> *band, int *d_err, cudaStream_t s) {
   constexpr int NB = FactorCfg<T>::NB;
   const size_t ns = (size_t)n * (kl + ku + 1);
-  static int cap16 = -1, cap8 = -1;  // resident 16- and 8-CTA clusters
+  static int cap10 = -1, cap8 = -1;  // resident 10- and 8-CTA clusters
   const size_t fsmem = (size_t)(NB + kl) * (NB + 1) * sizeof(cx<T>);  // >= kl x NB of L21
   if constexpr (sizeof(T) == 4) {
     if (cap8 < 0) {
-      cap16 = factor_cluster_capacity<T, 16>();
+      cap10 = factor_cluster_capacity<T, 10>();
       cap8 = factor_cluster_capacity<T, 8>();
     }
-    if (band_factor_cluster_ok<T>(kl, ku) && fsmem <= 160 * 1024 && (cap16 >= ne || cap8 > 0)) {
-      // 16-CTA clusters when every factor slot gets one at once, else 8
-      if (cap16 >= ne)
-        k_band_factor_cluster<T, NB, 16><<<dim3(16, ne), FNT, fsmem, s>>>(n, kl, ku, band, ns, d_err);
+    if (band_factor_cluster_ok<T>(kl, ku) && fsmem <= 160 * 1024 && (cap10 >= ne || cap8 > 0)) {
+      // 10-CTA clusters (9 updating CTAs per panel) when every factor slot gets
+      // one at once, else 8; with the panel on the critical path, larger
+      // clusters gain nothing more (measured: 12 CTAs as 10, 92 ms for 8)
+      if (cap10 >= ne)
+        k_band_factor_cluster<T, NB, 10><<<dim3(10, ne), FNT, fsmem, s>>>(n, kl, ku, band, ns, d_err);
       else
         k_band_factor_cluster<T, NB, 8><<<dim3(8, ne), FNT, fsmem, s>>>(n, kl, ku, band, ns, d_err);
       note_launch();
