@@ -199,7 +199,7 @@ def run_ours(args, rank, world, local_rank):
     # DRAM bytes (read + write) per k_band_solve_tma launch at N = 300, the mean
     # of the 5 launches of one solve in the ncu capture summarised in
     # profiles/k_band_solve_tma_convdiff2d.md; None for other sizes or forms
-    solve_traffic = 23.99e9 if (n == 90000 and prec == F.PREC_FP32_IR) else None
+    solve_traffic = None  # re-taken below once captured for this revision
     roof = None
     if n_solve:
         avg = solve_ms / n_solve
@@ -213,7 +213,7 @@ def run_ours(args, rank, world, local_rank):
                               else "FP64 nominal 1.25 TFLOP/s")}
     # multi-shift residual: algorithmic bytes per launch (one side)
     xs = ne * n * m * 16
-    resid_bytes = xs + n * m * 16 + ne * n * m * 8 + n * m * 16 + wk.A.nnz * 12 + (n + 1) * 4
+    resid_bytes = xs + n * m * 16 + ne * n * m * 8 + wk.A.nnz * 12 + (n + 1) * 4
     spmm = None
     if n_resid:
         avg = resid_ms / n_resid

@@ -317,25 +317,28 @@ __device__ void block_reduce_sum2(double &a, double *red) {
 // barrier per rotation; the right rotations of the whole sweep are then
 // applied row by row (rows are independent) to H and to Z.
 __device__ __forceinline__ void givens(cxd a, cxd b, double &c, cxd &s) {
-  // (c, s) with c real, c^2 + |s|^2 = 1 and [c s; -conj(s) c] [a; b] = [r; 0]
+  // (c, s) with c real, c^2 + |s|^2 = 1 and [c s; -conj(s) c] [a; b] = [r; 0]:
+  // c = |a| / rho, s = a conj(b) / (|a| rho), rho^2 = |a|^2 + |b|^2.  The
+  // entries are scaled by a power of two (exact) near 1 / max|.|, and both
+  // |a| rho and c come from one reciprocal square root of |a|^2 rho^2.
   const double sc = fmax(fmax(fabs(a.re), fabs(a.im)), fmax(fabs(b.re), fabs(b.im)));
   if (sc == 0.0) {
     c = 1.0;
     s = mk(0.0, 0.0);
     return;
   }
-  const double inv = 1.0 / sc;
+  const double inv = scalbn(1.0, -ilogb(sc));
   const cxd as = inv * a, bs = inv * b;
   const double aa2 = abs2(as), t = aa2 + abs2(bs);
-  const double rr = rsqrt(t);
-  if (aa2 == 0.0) {
-    c = 0.0;
-    s = mk(bs.re * rr, -bs.im * rr);
+  if (aa2 < 1e-280) {  // |a| negligible (or zero) next to |b|
+    const double rr = rsqrt(t), ra = aa2 > 0.0 ? rsqrt(aa2) : 0.0;
+    c = aa2 * ra * rr;
+    s = aa2 > 0.0 ? (ra * rr) * (as * conj(bs)) : mk(bs.re * rr, -bs.im * rr);
     return;
   }
-  const double ra = rsqrt(aa2);
-  c = aa2 * ra * rr;
-  s = (ra * rr) * (as * conj(bs));
+  const double r1 = rsqrt(aa2 * t);
+  c = aa2 * r1;
+  s = r1 * (as * conj(bs));
 }
 
 __global__ void __launch_bounds__(256, 1) k_small_eig(const cxd *A, int m, cxd *lam, cxd *V, cxd *work, int *err,

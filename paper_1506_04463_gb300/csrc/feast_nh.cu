@@ -288,10 +288,17 @@ void do_filter(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, cxd *Q, cxd *Qh, 
     ctx->inner_steps = 1;
   } else {
     CKC(cudaMemsetAsync(ctx->d_done, 0, sizeof(int), ctx->s));
+    // the first solve takes the right-hand sides in single precision (the
+    // factors' precision; the refinement restores the rest): they are staged
+    // in the first n x m entries of the residual buffers, which the first
+    // residual overwrites
+    launch_to_cxf(BY, (cxf *)ctx->Rn, (size_t)n * m, ctx->s);
+    if (!cs) launch_to_cxf(BhYh, (cxf *)ctx->Rhn, (size_t)n * m, ctx->s);
     int k0 = ev_begin(ctx, ctx->ev_solve);
-    CKC(band_solve_sides<float, double>(n, ctx->klp, ctx->kup, ne, ctx->fmap.data(), (const cxf *)ctx->band,
-                                        (const cxf *)ctx->dinv, BY, BhYh, 0, m, ctx->Xn, cs ? nullptr : ctx->Xhn,
-                                        xns, 0, (cxf *)ctx->ysc, nullptr, ctx->s, tma_ptr(ctx), ctx->d_err));
+    CKC(band_solve_sides<float, float>(n, ctx->klp, ctx->kup, ne, ctx->fmap.data(), (const cxf *)ctx->band,
+                                       (const cxf *)ctx->dinv, (const cxf *)ctx->Rn,
+                                       cs ? nullptr : (const cxf *)ctx->Rhn, 0, m, ctx->Xn, cs ? nullptr : ctx->Xhn,
+                                       xns, 0, (cxf *)ctx->ysc, nullptr, ctx->s, tma_ptr(ctx), ctx->d_err));
     ev_end(ctx, ctx->ev_solve, k0);
     int g = launch_colnorm2(BY, m, m, n, ctx->colp, ctx->s);
     launch_reduce_parts(ctx->colp, g, m, ctx->bynorm2, ctx->s);
@@ -302,13 +309,14 @@ void do_filter(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, cxd *Q, cxd *Qh, 
     const int steps = ctx->o.inner_max < 1 ? 1 : ctx->o.inner_max;
     for (int it = 0; it < steps; ++it) {
       int kr = ev_begin(ctx, ctx->ev_resid);
+      // residuals only: the node sum Q is formed once, from the final X
       const int gm = launch_multishift_residual<float>(ctx->A, Bp, ne, ctx->dz, ctx->dw, ctx->Xn, BY, (cxf *)ctx->Rn,
-                                                       Q, ctx->part, m, nullptr, ctx->s);
+                                                       nullptr, ctx->part, m, nullptr, ctx->s);
       ev_end(ctx, ctx->ev_resid, kr);
       if (!cs) {
         kr = ev_begin(ctx, ctx->ev_resid);
-        launch_multishift_residual<float>(ctx->AH, BHp, ne, ctx->dzc, ctx->dwc, ctx->Xhn, BhYh, (cxf *)ctx->Rhn, Qh,
-                                          ctx->part + (size_t)gm * ne * m, m, nullptr, ctx->s);
+        launch_multishift_residual<float>(ctx->AH, BHp, ne, ctx->dzc, ctx->dwc, ctx->Xhn, BhYh, (cxf *)ctx->Rhn,
+                                          nullptr, ctx->part + (size_t)gm * ne * m, m, nullptr, ctx->s);
         ev_end(ctx, ctx->ev_resid, kr);
       }
       launch_residual_check(ctx->part, gm, ne, m, ctx->bynorm2, cs ? 1 : 2, inner_tol, ctx->d_maxrel, ctx->d_done,
@@ -330,6 +338,8 @@ void do_filter(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, cxd *Q, cxd *Qh, 
         ev_end(ctx, ctx->ev_solve, ks);
       }
     }
+    launch_node_sum(ne, ctx->dw, ctx->Xn, xns, n, m, Q, ctx->s);
+    if (!cs) launch_node_sum(ne, ctx->dwc, ctx->Xhn, xns, n, m, Qh, ctx->s);
   }
   if (cs) launch_copy_conj(Q, Qh, (size_t)n * m, ctx->s);
   check_launch(ctx, "contour integration");

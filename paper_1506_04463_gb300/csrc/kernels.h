@@ -41,6 +41,9 @@ template <typename T> bool band_fits(int kl, int ku);
 template <typename T> bool band_solve_fits(int kl, int ku);
 
 // ---------------- spmm.cu : sparse products --------------------------------
+// Q = sum_j w_j X_j over the node-major blocks X; complex128 -> complex64 copy
+void launch_node_sum(int ne, const cxd *d_w, const cxd *X, size_t xns, int n, int m, cxd *Q, cudaStream_t s);
+void launch_to_cxf(const cxd *X, cxf *Y, size_t count, cudaStream_t s);
 // R_j = BY - (z_j B - A) X_j for all nodes j (node-major X, R), optional
 // Q = sum_j w_j X_j, per-CTA partial sums of |R_j,c|^2 into partial
 // [gridDim][ne*m].  Returns the grid size used (for the reduction).

@@ -70,8 +70,10 @@ __global__ void __launch_bounds__(kMsThreads)
         }
         cfms(acc, zs[j], bx);
         for (int64_t k = ka; k < kae; ++k) csr_fma<ACPLX>(acc, A, k, Xj[(size_t)A.colind[k] * m + c]);
-        if (R) R[(size_t)j * xns + (size_t)i * m + c] = ccast<Tout>(acc);
-        nacc[q] += abs2(acc);
+        const cx<Tout> ro = ccast<Tout>(acc);
+        if (R) R[(size_t)j * xns + (size_t)i * m + c] = ro;
+        // the norm of the stored residual, squared in its own precision
+        nacc[q] += (double)(ro.re * ro.re + ro.im * ro.im);
       }
     }
     if (Q) {
@@ -89,6 +91,34 @@ __global__ void __launch_bounds__(kMsThreads)
       if (pair < P) partial[(size_t)blockIdx.x * P + pair] = nacc[q];
     }
   }
+}
+
+// Q = sum_j w_j X_j (eq. q00 with the nodes' solutions), row-major n x m,
+// nodes summed in fixed order
+__global__ void k_node_sum(int ne, const cxd *__restrict__ w, const cxd *__restrict__ X, size_t xns, size_t nm,
+                           cxd *__restrict__ Q) {
+  __shared__ cxd ws[kMaxNe];
+  if (threadIdx.x < ne) ws[threadIdx.x] = w[threadIdx.x];
+  __syncthreads();
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nm; e += (size_t)gridDim.x * blockDim.x) {
+    cxd q = mk(0.0, 0.0);
+    for (int j = 0; j < ne; ++j) cfma(q, ws[j], X[(size_t)j * xns + e]);
+    Q[e] = q;
+  }
+}
+void launch_node_sum(int ne, const cxd *d_w, const cxd *X, size_t xns, int n, int m, cxd *Q, cudaStream_t s) {
+  const size_t nm = (size_t)n * m;
+  k_node_sum<<<grid_for(nm), 256, 0, s>>>(ne, d_w, X, xns, nm, Q);
+  note_launch();
+}
+// complex128 -> complex64 copy (single-precision right-hand sides)
+__global__ void k_to_cxf(const cxd *__restrict__ X, cxf *__restrict__ Y, size_t count) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+    Y[e] = ccast<float>(X[e]);
+}
+void launch_to_cxf(const cxd *X, cxf *Y, size_t count, cudaStream_t s) {
+  k_to_cxf<<<grid_for(count), 256, 0, s>>>(X, Y, count);
+  note_launch();
 }
 
 int spmm_max_grid() {
