@@ -199,7 +199,7 @@ def run_ours(args, rank, world, local_rank):
     # DRAM bytes (read + write) per k_band_solve_tma launch at N = 300, the mean
     # of the 5 launches of one solve in the ncu capture summarised in
     # profiles/k_band_solve_tma_convdiff2d.md; None for other sizes or forms
-    solve_traffic = None  # re-taken below once captured for this revision
+    solve_traffic = 29.11e9 if (n == 90000 and prec == F.PREC_FP32_IR) else None
     roof = None
     if n_solve:
         avg = solve_ms / n_solve
