@@ -2,8 +2,9 @@
 //
 //  * k_multishift_residual: one pass over A (and B) applies every shift z_j
 //    to every column: R_j = B Y - (z_j B - A) X_j, the residual of the shifted
-//    systems of eq. (qr) for all quadrature nodes at once, and accumulates the
-//    filtered block Q = sum_j w_j X_j (eq. qr) in fixed node order.
+//    systems of eq. (qr) for all quadrature nodes at once, and optionally
+//    the filtered block Q = sum_j w_j X_j (eq. qr) in fixed node order.
+//  * k_node_sum: Q = sum_j w_j X_j alone, once per filter in the refined form.
 //  * k_spmm: Out = M1 X - s_c M2 X with a per-column shift, used for B Q,
 //    A U, B U and the eigen-residuals of eq. (res).
 //  * csr transpose for the conjugate-transpose products A^H, B^H (eq. ql and
