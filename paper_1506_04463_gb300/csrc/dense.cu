@@ -321,6 +321,16 @@ __device__ __forceinline__ void givens(cxd a, cxd b, double &c, cxd &s) {
   // c = |a| / rho, s = a conj(b) / (|a| rho), rho^2 = |a|^2 + |b|^2.  The
   // entries are scaled by a power of two (exact) near 1 / max|.|, and both
   // |a| rho and c come from one reciprocal square root of |a|^2 rho^2.
+  {
+    // usual magnitudes: |a|^2 |a|^2+|b|^2 far from over- and underflow, no scaling
+    const double aa2 = abs2(a), t = aa2 + abs2(b);
+    if (aa2 > 1e-140 && t < 1e140) {
+      const double r1 = rsqrt(aa2 * t);
+      c = aa2 * r1;
+      s = r1 * (a * conj(b));
+      return;
+    }
+  }
   const double sc = fmax(fmax(fabs(a.re), fabs(a.im)), fmax(fabs(b.re), fabs(b.im)));
   if (sc == 0.0) {
     c = 1.0;
