@@ -504,19 +504,33 @@ __global__ void __launch_bounds__(256, 1) k_small_eig(const cxd *A, int m, cxd *
   int its = 0, total = 0;
   const int maxtotal = 40 * m;
   while (true) {
-    if (tid == 0) {
+    if (tid < 32) {
+      // warp 0 runs the deflation test and the shift with the same values in
+      // every lane (lane 0 writes the results): the largest l <= hi whose
+      // subdiagonal is negligible, 32 candidates per vote, 0 if none
       const int hi = sh_hi;
-      int l = hi;
-      while (l > 0) {
-        const double s = cabs1(H[(size_t)(l - 1) * ld + l - 1]) + cabs1(H[(size_t)l * ld + l]);
-        const double sub = cabs1(H[(size_t)l * ld + l - 1]);
-        if (sub <= DBL_EPSILON * s || (its >= 20 && sub <= hfloor) || sub < 1e-300) break;
-        --l;
+      int l = 0;
+      for (int base = hi; base >= 1; base -= 32) {
+        const int lc = base - lane;
+        bool neg = false;
+        if (lc >= 1) {
+          const double s = cabs1(H[(size_t)(lc - 1) * ld + lc - 1]) + cabs1(H[(size_t)lc * ld + lc]);
+          const double sub = cabs1(H[(size_t)lc * ld + lc - 1]);
+          neg = sub <= DBL_EPSILON * s || (its >= 20 && sub <= hfloor) || sub < 1e-300;
+        }
+        const unsigned vote = __ballot_sync(0xffffffffu, neg);
+        if (vote) {
+          l = base - (__ffs(vote) - 1);
+          break;
+        }
       }
-      if (l > 0) H[(size_t)l * ld + l - 1] = mk(0.0, 0.0);
-      sh_l = l;
+      __syncwarp();
+      if (lane == 0) {
+        if (l > 0) H[(size_t)l * ld + l - 1] = mk(0.0, 0.0);
+        sh_l = l;
+      }
       if (l == hi) {
-        sh_hi = hi - 1;
+        if (lane == 0) sh_hi = hi - 1;
         its = 0;
       } else {
         ++its;
@@ -533,13 +547,14 @@ __global__ void __launch_bounds__(256, 1) k_small_eig(const cxd *A, int m, cxd *
           const cxd m1 = mid + disc, m2 = mid - disc;
           mu = abs2(m1 - d) < abs2(m2 - d) ? m1 : m2;
         }
-        sh_mu = mu;
-        if (total > maxtotal) {
+        if (lane == 0) sh_mu = mu;
+        if (total > maxtotal && lane == 0) {
           atomicOr(err, DEVERR_QR_NOCONV);
           sh_done = 1;
         }
       }
-      if (sh_hi < 1) sh_done = 1;
+      __syncwarp();
+      if (lane == 0 && sh_hi < 1) sh_done = 1;
     }
     __syncthreads();
     if (sh_done) break;
