@@ -220,6 +220,18 @@ void small_mm(const cxd *A, int opA, const cxd *B, int opB, cxd *C, int m, int k
   note_launch();
 }
 
+__device__ __forceinline__ double cabs1(cxd a) { return fabs(a.re) + fabs(a.im); }
+// 1 / d for d != 0, scaled by a power of two (exact) so |d|^2 cannot over- or
+// underflow; one FP64 division instead of the two of a complex quotient
+__device__ __forceinline__ cxd crecip(cxd d) {
+  const double sc = fmax(fabs(d.re), fabs(d.im));
+  const int e = ilogb(sc);
+  const double f = scalbn(1.0, -e);
+  const cxd ds = mk(d.re * f, d.im * f);
+  const double r = f / abs2(ds);
+  return mk(ds.re * r, -ds.im * r);
+}
+
 // ---------------------------------------------------------------------------
 // Gauss-Jordan inverse with partial pivoting (one CTA)
 // ---------------------------------------------------------------------------
@@ -228,6 +240,7 @@ __global__ void __launch_bounds__(512) k_small_inv(const cxd *A, int m, cxd *Ain
   __shared__ double bv[512];
   __shared__ int bi[512];
   __shared__ int piv_s;
+  __shared__ cxd dinv_s;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int e = tid; e < m * m; e += nt) {
     W[e] = A[e];
@@ -239,7 +252,7 @@ __global__ void __launch_bounds__(512) k_small_inv(const cxd *A, int m, cxd *Ain
     double best = -1.0;
     int bidx = p;
     for (int i = p + tid; i < m; i += nt) {
-      double v = cabs(W[(size_t)i * m + p]);
+      double v = cabs1(W[(size_t)i * m + p]);  // |re| + |im|, as in LAPACK's pivot search
       if (v > best) { best = v; bidx = i; }
     }
     bv[tid] = best;
@@ -271,11 +284,15 @@ __global__ void __launch_bounds__(512) k_small_inv(const cxd *A, int m, cxd *Ain
       }
     }
     __syncthreads();
-    const cxd d = W[(size_t)p * m + p];
+    if (tid == 0) {
+      const cxd d = W[(size_t)p * m + p];
+      dinv_s = (d.re != 0.0 || d.im != 0.0) ? crecip(d) : mk(0.0, 0.0);
+    }
     __syncthreads();
+    const cxd dinv = dinv_s;
     for (int j = tid; j < m; j += nt) {
-      W[(size_t)p * m + j] = cdiv(W[(size_t)p * m + j], d);
-      Ainv[(size_t)p * m + j] = cdiv(Ainv[(size_t)p * m + j], d);
+      W[(size_t)p * m + j] = W[(size_t)p * m + j] * dinv;
+      Ainv[(size_t)p * m + j] = Ainv[(size_t)p * m + j] * dinv;
     }
     for (int i = tid; i < m; i += nt) f[i] = W[(size_t)i * m + p];
     __syncthreads();
@@ -296,19 +313,7 @@ void small_inv(const cxd *A, int m, cxd *Ainv, cxd *work, int *d_err, cudaStream
 // ---------------------------------------------------------------------------
 // eigendecomposition of a general complex m x m matrix (one CTA)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double cabs1(cxd a) { return fabs(a.re) + fabs(a.im); }
 
-__device__ void block_reduce_sum2(double &a, double *red) {
-  const int tid = threadIdx.x;
-  red[tid] = a;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o; o >>= 1) {
-    if (tid < o) red[tid] += red[tid + o];
-    __syncthreads();
-  }
-  a = red[0];
-  __syncthreads();
-}
 
 // work layout: H (m*m; used when H does not fit in shared memory), Z (m*m), E (m*m).
 // H lives in dynamic shared memory (odd row stride) when it fits.  The QR
@@ -361,6 +366,9 @@ __global__ void __launch_bounds__(256, 1) k_small_eig(const cxd *A, int m, cxd *
   __shared__ int sh_l, sh_hi, sh_done;
   __shared__ cxd sh_mu;
   __shared__ double dsc[kMaxM0];  // balancing: H = D^{-1} A D, D = diag(dsc)
+  __shared__ int hskip_s;         // Householder step: reflector scalars from warp 0
+  __shared__ double hsc_s;
+  __shared__ cxd hbeta_s;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
   const int ld = hsm ? (m | 1) : m;
   cxd *H = hsm ? reinterpret_cast<cxd *>(dsm) : work;
@@ -424,23 +432,40 @@ __global__ void __launch_bounds__(256, 1) k_small_eig(const cxd *A, int m, cxd *
   // ---- Householder reduction to upper Hessenberg form: H = Z^H A Z ----
   for (int k = 0; k + 2 < m; ++k) {
     const int L = m - k - 1;
-    double nrm2 = 0.0;
-    for (int i = tid; i < L; i += nt) nrm2 += abs2(H[(size_t)(k + 1 + i) * ld + k]);
-    block_reduce_sum2(nrm2, red);
-    if (nrm2 == 0.0) continue;
-    const double nrm = sqrt(nrm2);
-    const cxd x0 = H[(size_t)(k + 1) * ld + k];
-    const double ax0 = cabs(x0);
-    const cxd ph = ax0 > 0 ? mk(x0.re / ax0, x0.im / ax0) : mk(1.0, 0.0);
-    const cxd beta = mk(-ph.re * nrm, -ph.im * nrm);
+    // the reflector's scalars, once, in warp 0 (an FP64 instruction costs the
+    // same for one lane as for 32, so redundant copies in every warp are not free)
+    if (tid < 32) {
+      double nrm2 = 0.0;
+      for (int i = lane; i < L; i += 32) nrm2 += abs2(H[(size_t)(k + 1 + i) * ld + k]);
+#pragma unroll
+      for (int o = 16; o; o >>= 1) nrm2 += __shfl_xor_sync(0xffffffffu, nrm2, o);
+      if (lane == 0) {
+        int skip = nrm2 == 0.0;
+        cxd beta = mk(0.0, 0.0);
+        double sc = 0.0;
+        if (!skip) {
+          const double nrm = sqrt(nrm2);
+          const cxd x0 = H[(size_t)(k + 1) * ld + k];
+          const double ax0 = cabs(x0);
+          const cxd ph = ax0 > 0 ? mk(x0.re / ax0, x0.im / ax0) : mk(1.0, 0.0);
+          beta = mk(-ph.re * nrm, -ph.im * nrm);
+          // |v|^2 = nrm2 - |x0|^2 + |x0 - beta|^2
+          const double vn2 = nrm2 - abs2(x0) + abs2(x0 - beta);
+          skip = vn2 == 0.0;
+          if (!skip) sc = 2.0 / vn2;
+        }
+        hskip_s = skip;
+        hsc_s = sc;
+        hbeta_s = beta;
+      }
+    }
     for (int i = tid; i < L; i += nt) v[i] = H[(size_t)(k + 1 + i) * ld + k];
     __syncthreads();
+    if (hskip_s) continue;
+    const cxd beta = hbeta_s;
+    const double sc = hsc_s;
     if (tid == 0) v[0] = v[0] - beta;
     __syncthreads();
-    // |v|^2 = nrm2 - |x0|^2 + |x0 - beta|^2
-    const double vn2 = nrm2 - abs2(x0) + abs2(x0 - beta);
-    if (vn2 == 0.0) continue;
-    const double sc = 2.0 / vn2;
     // left: H[k+1.., j] -= v (v^H H[k+1.., j]) sc, four threads per column
     for (int base = 0; base < m - k; base += nt >> 2) {  // uniform trip count: all lanes shuffle
       const int jj = base + (tid >> 2), j = k + jj, part = tid & 3;
@@ -643,7 +668,7 @@ __global__ void __launch_bounds__(256, 1) k_small_eig(const cxd *A, int m, cxd *
       for (int l2 = j + 1; l2 <= k; ++l2) cfma(s, H[(size_t)j * ld + l2], E[(size_t)l2 * m + k]);
       cxd d = H[(size_t)j * ld + j] - tk;
       if (cabs1(d) < small) d = mk(small, 0.0);
-      E[(size_t)j * m + k] = -cdiv(s, d);
+      E[(size_t)j * m + k] = -(s * crecip(d));
     }
     lam[k] = tk;
   }
