@@ -543,10 +543,12 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(FNT)
           L11[r][p] = (r < nb && p < r && r - p <= kl) ? ldcg(Bd + (size_t)(k + r) * W + (p - r + kl)) : mk<T>(0, 0);
         }
         const int tot = nrows * NB;
-        for (int e0 = tid; e0 < tot; e0 += UNR * FNT) {
-          cx<T> v[UNR];
+        // all of L21 (kl x 32 entries, <= 20 per thread at kl <= 300) in flight at once
+        constexpr int UNR2 = 20;
+        for (int e0 = tid; e0 < tot; e0 += UNR2 * FNT) {
+          cx<T> v[UNR2];
 #pragma unroll
-          for (int u = 0; u < UNR; ++u) {
+          for (int u = 0; u < UNR2; ++u) {
             const int e = e0 + u * FNT;
             const int rr = e / NB, p = e - rr * NB;
             const int r = c_beg + rr;
@@ -554,7 +556,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(FNT)
                                                             : mk<T>(0, 0);
           }
 #pragma unroll
-          for (int u = 0; u < UNR; ++u) {
+          for (int u = 0; u < UNR2; ++u) {
             const int e = e0 + u * FNT;
             if (e < tot) Ls[e] = v[u];
           }
