@@ -10,8 +10,8 @@ test, output) from the same start blocks; the metric is converged eigenpairs
 (eq. res <= 1e-10) per second.
 
 --impl reference times the CPU oracle (the plain FP64 algorithm, scipy
-SuperLU per node) on a bounded sample of the same workload and extrapolates
-to one full solve.
+SuperLU per node) on complete solves of the same workload, its shifted solves
+spread over the host cores by node.
 """
 from __future__ import annotations
 
@@ -196,9 +196,10 @@ def run_ours(args, rank, world, local_rank):
     solve_flops = 2 * ne * m * (n * (kl + ku)) * 8.0
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12       # TFLOP/s at the max SM clock
     fp64_peak = 1.25                                          # nominal FP64 TFLOP/s of the part
-    # DRAM bytes (read + write) per k_band_solve_tma launch at N = 300, the mean
-    # of the 5 launches of one solve in the ncu capture summarised in
-    # profiles/k_band_solve_tma_convdiff2d.md; None for other sizes or forms
+    # DRAM bytes (read + write) per k_band_solve_tma launch at N = 300: the
+    # mean over the 5 launches of one solve in an ncu capture of the current
+    # kernel (dram__bytes_read.sum + dram__bytes_write.sum); None for other
+    # sizes or forms, where no capture was taken
     solve_traffic = 29.11e9 if (n == 90000 and prec == F.PREC_FP32_IR) else None
     roof = None
     if n_solve:
@@ -207,7 +208,9 @@ def run_ours(args, rank, world, local_rank):
         peak = fp32_peak if prec == F.PREC_FP32_IR else fp64_peak
         roof = {"kernel": "k_band_solve_tma" if prec == F.PREC_FP32_IR else "k_band_solve",
                 "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-                "frac": round(ach / peak, 4), "traffic": solve_traffic, "avg_launch_ms": round(avg, 3),
+                "frac": round(ach / peak, 4), "traffic": solve_traffic,
+                "traffic_source": "ncu capture of this kernel (dram bytes read+write per launch), not this run",
+                "avg_launch_ms": round(avg, 3),
                 "launches": n_solve, "flops_per_launch": solve_flops,
                 "peak_note": ("FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock" if prec == F.PREC_FP32_IR
                               else "FP64 nominal 1.25 TFLOP/s")}
@@ -246,13 +249,20 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         pms = e0.elapsed_time(e1)
         plain = {"eigenpairs_per_s": round(o["m"] / (pms / 1e3), 3), "ms_per_solve": round(pms, 1), "m": o["m"],
+                 "_lam": o["lam"].cpu().numpy(), "_res": o["res"].cpu().numpy(),
                  "max_res": float(o["res"].max().item()) if o["m"] else None,
                  "speedup_chosen_over_plain": round(value / world / (o["m"] / (pms / 1e3)), 3)}
         ctxp.close()
 
-    cpu = None
+    cpu, pairs_err = None, None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(wk, iterations=inf["iterations"])
+        cpu, ref = cpu_baseline(wk)
+        pairs_err = {"chosen": per_pair_errors(out["lam"].cpu().numpy(), out["res"].cpu().numpy(), ref)}
+        if plain is not None:
+            pairs_err["plain_fp64"] = per_pair_errors(plain.pop("_lam"), plain.pop("_res"), ref)
+    if plain is not None:
+        plain.pop("_lam", None)
+        plain.pop("_res", None)
 
     ctx.close()
     if rank != 0:
@@ -269,6 +279,7 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "256 MB buffer written between timed steps; working set > L2"},
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "spmm": spmm, "kernel_ms_per_step": kernel_times,
         "cpu_baseline": cpu, "clocks": clocks, "plain_fp64": plain,
+        "per_eigenpair_vs_fp64_oracle": pairs_err,
         "check": {"m": int(ms_found[-1]), "iterations": inf["iterations"], "max_res": max_res,
                   "inner_steps_last_filter": inf["inner_steps"], "inner_res": inf["inner_res"],
                   "max_rel_eig_err_vs_closed_form": eig_err},
@@ -320,32 +331,153 @@ def e2e_measure(args, wk, dev, prec, F, torch):
 
 
 # ----------------------------------------------------------------------------
-# CPU oracle leg
+# CPU oracle leg: the oracle's complete solve (Fig. alg:three, FP64), with its
+# shifted solves spread over the host cores: one spawned worker process per
+# group of nodes keeps that group's SuperLU factors (the saved-factorisation
+# option of Sec. 4.1) and solves the right-hand sides it is sent through shared
+# memory; the oracle itself sums the solutions in node order and runs the
+# Rayleigh-Ritz step with numpy's threaded BLAS.
 # ----------------------------------------------------------------------------
-def oracle_sample(wk, iterations, sample_nodes=1):
-    """Time the oracle on `sample_nodes` of the ne nodes (SuperLU factorisation,
-    right and left solves with m0 columns) plus one Rayleigh-Ritz step, and
-    extrapolate to a full solve with `iterations` outer iterations:
-        T = ne*t_fact + iterations*(ne*t_solve + t_rr)."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True,
+                             timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def _node_worker(conn, nodes, a_parts, b_parts, z, rhs_name, out_name, n, m0, ne):
+    import numpy as _np
+    import scipy.sparse as _sp
+    from multiprocessing import shared_memory
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
     from oracle import feast_nh as OF
-    from oracle.contour import contour_nodes
-    z, w = contour_nodes(wk.contour)
+    A = _sp.csr_matrix(tuple(a_parts[:3]), shape=a_parts[3])
+    B = None if b_parts is None else _sp.csr_matrix(tuple(b_parts[:3]), shape=b_parts[3])
+    rhs_shm = shared_memory.SharedMemory(name=rhs_name)
+    out_shm = shared_memory.SharedMemory(name=out_name)
+    rhs_all = _np.ndarray((n * m0,), _np.complex128, buffer=rhs_shm.buf)
+    out_all = _np.ndarray((ne, n * m0), _np.complex128, buffer=out_shm.buf)
+    solvers = {}
+    try:
+        while True:
+            msg = conn.recv()
+            if msg[0] == "factor":
+                for j in nodes:
+                    solvers[j] = OF.NodeSolver(A, B, z[j], dense=False)
+                conn.send("ok")
+            elif msg[0] == "solve":
+                _, m, herm = msg
+                rhs = rhs_all[: n * m].reshape(n, m)
+                for j in nodes:
+                    out_all[j, : n * m].reshape(n, m)[...] = solvers[j].solve(rhs, herm=herm)
+                conn.send("ok")
+            else:
+                break
+    finally:
+        del rhs_all, out_all
+        rhs_shm.close()
+        out_shm.close()
+
+
+class ParallelNodeSolvers:
+    """The oracle's per-node solvers (scipy SuperLU, FP64) in `workers` spawned
+    processes; solve_all(rhs, herm) returns every node's solution in node order
+    (views into shared memory, valid until the next call)."""
+
+    def __init__(self, A, B, z, m0, workers=None):
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+        ne, n = len(z), A.shape[0]
+        self.ne, self.n, self.m0 = ne, n, m0
+        self.workers = max(1, min(ne, workers or host_cores()))
+        self.rhs_shm = shared_memory.SharedMemory(create=True, size=n * m0 * 16)
+        self.out_shm = shared_memory.SharedMemory(create=True, size=ne * n * m0 * 16)
+        self.rhs = np.ndarray((n * m0,), np.complex128, buffer=self.rhs_shm.buf)
+        self.out = np.ndarray((ne, n * m0), np.complex128, buffer=self.out_shm.buf)
+        A = A.tocsr()
+        a_parts = (A.data, A.indices, A.indptr, A.shape)
+        b_parts = None if B is None else (B.tocsr().data, B.tocsr().indices, B.tocsr().indptr, B.shape)
+        ctx = mp.get_context("spawn")
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        os.environ.update(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        self.procs, self.conns = [], []
+        try:
+            for k in range(self.workers):
+                nodes = list(range(k, ne, self.workers))
+                a, b = ctx.Pipe()
+                p = ctx.Process(target=_node_worker, args=(b, nodes, a_parts, b_parts, np.asarray(z),
+                                                           self.rhs_shm.name, self.out_shm.name, n, m0, ne),
+                                daemon=True)
+                p.start()
+                self.procs.append(p)
+                self.conns.append(a)
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        self.t_solve = 0.0
+
+    def _all(self, msg):
+        for c in self.conns:
+            c.send(msg)
+        for c in self.conns:
+            if c.recv() != "ok":
+                raise RuntimeError("oracle worker failed")
+
+    def factor(self):
+        self._all(("factor",))
+
+    def solve_all(self, rhs, herm=False):
+        t0 = time.perf_counter()
+        n, m = rhs.shape
+        self.rhs[: n * m].reshape(n, m)[...] = rhs
+        self._all(("solve", m, bool(herm)))
+        self.t_solve += time.perf_counter() - t0
+        return [self.out[j, : n * m].reshape(n, m) for j in range(self.ne)]
+
+    def close(self):
+        for c in self.conns:
+            try:
+                c.send(("stop",))
+            except Exception:
+                pass
+        for p in self.procs:
+            p.join(timeout=30)
+        del self.rhs, self.out
+        self.rhs_shm.close()
+        self.rhs_shm.unlink()
+        self.out_shm.close()
+        self.out_shm.unlink()
+
+
+def oracle_full_solve(wk, pool):
+    """One complete oracle solve of the workload (factorisations included)."""
+    from oracle import feast_nh as OF
+    pool.t_solve = 0.0
     t0 = time.perf_counter()
-    solvers = [OF.NodeSolver(wk.A, None, z[j], dense=False) for j in range(sample_nodes)]
+    pool.factor()
     t1 = time.perf_counter()
-    Q = np.zeros(wk.Y0.shape, np.complex128)
-    Qh = np.zeros(wk.Y0.shape, np.complex128)
-    for j, s in enumerate(solvers):
-        Q += w[j] * s.solve(wk.Y0)
-        Qh += np.conj(w[j]) * s.solve(wk.Yh0, herm=True)
+    out = OF.feast_nh(wk.A, wk.B, wk.contour, wk.m0, wk.Y0, wk.Yh0, solvers=pool)
     t2 = time.perf_counter()
-    OF.rayleigh_ritz(wk.A, None, Q, Qh, z, w)
-    t3 = time.perf_counter()
-    ne = len(z)
-    t_fact = (t1 - t0) / sample_nodes
-    t_solve = (t2 - t1) / sample_nodes
-    T = ne * t_fact + iterations * (ne * t_solve + (t3 - t2))
-    return T, dict(t_fact=t_fact, t_solve=t_solve, t_rr=t3 - t2, sample_s=t3 - t0)
+    phases = {"factor_s": round(t1 - t0, 3), "shifted_solves_s": round(pool.t_solve, 3),
+              "rayleigh_ritz_and_rest_s": round(t2 - t1 - pool.t_solve, 3), "total_s": round(t2 - t0, 3)}
+    return out, phases
 
 
 def threads_used():
@@ -356,39 +488,74 @@ def threads_used():
         return os.cpu_count() or 1
 
 
-def cpu_baseline(wk, iterations):
-    T, d = oracle_sample(wk, iterations)
-    m = wk.exact.size
-    return {"value": round(m / T, 5), "unit": UNIT, "cores": threads_used(), "kind": "oracle",
-            "sample": (f"oracle (scipy SuperLU per node + numpy RR, FP64) on 1 of {wk.contour.ne} nodes and one "
-                       f"Rayleigh-Ritz step of the same workload ({d['sample_s']:.1f} s), extrapolated to "
-                       f"ne={wk.contour.ne} factorisations + {iterations} iterations x (ne solves + RR) = "
-                       f"{T:.1f} s for m={m}"),
-            "per_phase_s": {k: round(v, 3) for k, v in d.items()}}
+def cpu_baseline(wk):
+    """The oracle's complete solve of the bench workload on the host cores."""
+    pool = ParallelNodeSolvers(wk.A, wk.B, __import__("oracle.contour", fromlist=["x"]).contour_nodes(wk.contour)[0],
+                               wk.m0)
+    try:
+        out, ph = oracle_full_solve(wk, pool)
+    finally:
+        pool.close()
+    T = ph["total_s"]
+    line = {"value": round(out["m"] / T, 5), "unit": UNIT, "cores": pool.workers, "kind": "oracle",
+            "sample": (f"full oracle solve of the same workload (FP64, scipy SuperLU per node, {out['iterations']} "
+                       f"outer iterations, m={out['m']}): {pool.workers} worker processes hold the ne="
+                       f"{wk.contour.ne} node factorisations and run the shifted solves in parallel; Rayleigh-Ritz "
+                       f"with numpy BLAS ({threads_used()} threads)"),
+            "per_phase_s": ph, "nproc": host_cores(), "cpu_model": cpu_model(), "iterations": out["iterations"]}
+    return line, out
+
+
+def per_pair_errors(lam_gpu, res_gpu, ref):
+    """|lambda_gpu - lambda_oracle| / |lambda_oracle| per eigenpair after an
+    optimal one-to-one matching, with each pair's eq. (res) residual."""
+    from scipy.optimize import linear_sum_assignment
+    lam_gpu, lo = np.asarray(lam_gpu), np.asarray(ref["lam"])
+    if lam_gpu.size == 0 or lo.size == 0:
+        return None
+    C = np.abs(lam_gpu[:, None] - lo[None, :])
+    r, c = linear_sum_assignment(C)
+    order = np.argsort(lo[c].real)
+    r, c = r[order], c[order]
+    err = C[r, c] / np.abs(lo[c])
+    return {"n_gpu": int(lam_gpu.size), "n_oracle": int(lo.size), "max_rel_err": float(err.max()),
+            "rel_err": [float(f"{e:.3g}") for e in err],
+            "res_gpu": [float(f"{v:.3g}") for v in np.asarray(res_gpu)[r]],
+            "res_oracle": [float(f"{v:.3g}") for v in np.asarray(ref["res"])[c]]}
 
 
 def run_reference(args, rank, world):
+    from oracle.contour import contour_nodes
     from paper_1506_04463_gb300 import workloads as wl
     if rank != 0:
         return None
     wk = wl.config2(N=args.N)
-    iters = 2  # outer iterations this workload needs (both forms of the GPU path and the oracle)
-    vals, samples = [], []
-    for k in range(args.warmup + args.steps):
-        T, d = oracle_sample(wk, iters)
-        if k >= args.warmup:
-            vals.append(wk.exact.size / T)
-            samples.append(d["sample_s"])
+    pool = ParallelNodeSolvers(wk.A, wk.B, contour_nodes(wk.contour)[0], wk.m0)
+    vals, phases, timed = [], None, 0
+    budget_s, t_start = 240.0, time.perf_counter()
+    try:
+        for k in range(args.warmup + args.steps):
+            out, ph = oracle_full_solve(wk, pool)
+            if k >= args.warmup:
+                vals.append(out["m"] / ph["total_s"])
+                phases = ph
+                timed += 1
+            # each step is a complete solve; stop early rather than overrun the budget
+            if time.perf_counter() - t_start > budget_s and timed >= 1:
+                break
+    finally:
+        pool.close()
     value = statistics.mean(vals)
-    ms = 1e3 * statistics.mean(samples)
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": True,
+            "steps": args.steps, "steps_timed": timed, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * out["m"] / value, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
             "config": {"workload": WORKLOAD, "form": "CPU oracle (plain FP64 algorithm)", "parallelism": "host cores"},
-            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": threads_used(), "kind": "oracle",
-                             "sample": ("each step: SuperLU of 1 of 16 shifted matrices, right+left solves with "
-                                        "64 columns and one Rayleigh-Ritz step; eigenpairs/s extrapolated to a full "
-                                        "solve of 16 factorisations + 2 iterations")},
+            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": pool.workers, "kind": "oracle",
+                             "sample": (f"each step: one complete oracle solve ({out['iterations']} outer iterations, "
+                                        f"m={out['m']}), the ne={wk.contour.ne} SuperLU factorisations and shifted "
+                                        f"solves spread over {pool.workers} worker processes"),
+                             "per_phase_s": phases, "nproc": host_cores(), "cpu_model": cpu_model()},
             "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     return line
 

@@ -21,10 +21,10 @@
  *    (n, m) and dtype complex128.  The caller owns them.
  *  - Small outputs `lambda` (complex, 2 doubles per entry) and `res` are
  *    DEVICE arrays of length m0; counts and the info struct are HOST memory.
- *  - All work is enqueued on the stream given to feast_nh_init.  feast_nh_filter
- *    and the block part of feast_nh_rr are asynchronous; feast_nh_rr and
- *    feast_nh_solve read a few integers back from the device (subspace size,
- *    counts, convergence flag) once per call / per outer iteration.
+ *  - All work is enqueued on the stream given to feast_nh_init.  feast_nh_filter,
+ *    feast_nh_rr and feast_nh_solve read a few numbers back from the device
+ *    (inner residual and error word, subspace size, counts, convergence flag)
+ *    once per call / per outer iteration / per refinement step.
  *  - The library allocates its workspace in feast_nh_init (and, for the
  *    banded factors, on the first filter) and frees it in feast_nh_destroy.
  *  - Errors are returned, never raised or aborted; feast_nh_last_error gives
@@ -119,6 +119,13 @@ typedef struct {
   int32_t n_factorizations; /* shifted matrices factorised: ne, or ne/2 for a
                                real pencil whose nodes come in conjugate pairs
                                (Sec. 2.4, Table tab:solve)                    */
+  int32_t inner_fail;       /* filters of this solve whose shifted solves
+                               stopped above their tolerance (refinement or
+                               Krylov cap reached)                            */
+  double pivot_min, pivot_max; /* smallest / largest pivot modulus |u_rr| of
+                               the banded factors (no pivoting is done: a
+                               tiny ratio flags factors that may be
+                               inaccurate; the refinement residual decides)   */
 } feast_nh_info;
 
 /* Fills *o with the defaults listed above. */
@@ -136,7 +143,11 @@ feast_nh_status feast_nh_init(feast_nh_ctx **ctx, const feast_nh_csr *A, const f
 /* Contour integration, step 1 of Fig. alg:three (eq. qr, eq. ql): from the
  * n x m blocks Y, Yh computes Q and Qh (m <= m0).  Yh/Qh may be NULL for the
  * complex-symmetric problem, where Qh = conj(Q) (Sec. 2.4).  Factorises the
- * shifted matrices on first use and keeps the factors (Sec. 4.1 option). */
+ * shifted matrices on first use and keeps the factors (Sec. 4.1 option).
+ * Waits for the stream once, to read the largest relative residual
+ * ||BY - (z_j B - A) X_j||_2 / ||BY||_2 of the shifted solves: above
+ * opts.inner_tol it returns FEAST_NH_EINNER (Q, Qh then hold the filter of the
+ * last iterates). */
 feast_nh_status feast_nh_filter(feast_nh_ctx *ctx, const void *Y, const void *Yh, void *Q, void *Qh,
                                 int32_t m);
 
@@ -155,7 +166,10 @@ feast_nh_status feast_nh_rr(feast_nh_ctx *ctx, const void *Q, const void *Qh, in
  * lambda (m0 complex) and res (m0 doubles, eq. res) are the converged
  * eigenpairs inside C, normalised with ||x_i||_2 = 1 (largest entry real
  * positive) and x^_i^H B x_i = 1.  Returns FEAST_NH_ENOCONV after
- * opts.max_iter outer iterations. */
+ * opts.max_iter outer iterations, or FEAST_NH_EINNER instead when some
+ * filter's shifted solves also stopped above their tolerance
+ * (info->inner_fail counts them; a converged solve returns FEAST_NH_OK and
+ * still reports the count). */
 feast_nh_status feast_nh_solve(feast_nh_ctx *ctx, const void *Y0, const void *Yh0, double *lambda,
                                void *X, void *Xh, double *res, int32_t *m_found, feast_nh_info *info);
 
@@ -179,9 +193,31 @@ feast_nh_status feast_nh_nodes(const feast_nh_contour *contour, double *z, doubl
  * measurement: for every node j and column c,
  *   R_j = B Y - (z_j B - A) X_j       and  Q = sum_j w_j X_j  (if Q != NULL)
  * with X (ne blocks of n x m, node-major, device complex double), Y (n x m),
- * R (ne blocks, device complex double).  One pass over A and B. */
+ * R (ne blocks, device).  Arithmetic in FP64; R is stored as complex double,
+ * or as complex float (interleaved) when r_single != 0, the form the refined
+ * single-precision solves read.  One pass over A and B (eq. qr). */
 feast_nh_status feast_nh_multishift_residual(feast_nh_ctx *ctx, const void *X, const void *BY, void *R,
-                                             void *Q, int32_t m);
+                                             void *Q, int32_t m, int32_t r_single);
+
+/* Eigen-decomposition of an m x m complex matrix M (device, row-major,
+ * 1 <= m <= 128) by the library's small dense eigensolver, the one used for
+ * B_Q = V Gamma V^^H (eq. bdiag, Sec. 2.5) and the reduced problem of step
+ * 4.b: lambda (m complex) and right eigenvectors V (m x m, row-major, column
+ * k for lambda_k), on ctx's stream with ctx's workspace.  Exposed so that the
+ * eigensolver can be tested on its own.  Waits for the stream; a QR sweep
+ * that does not converge returns FEAST_NH_ECUDA. */
+feast_nh_status feast_nh_small_eig(feast_nh_ctx *ctx, const void *M, int32_t m, void *lambda, void *V);
+
+/* Device error-word bits, as reported through the status codes. */
+enum { FEAST_NH_DEVERR_ZERO_PIVOT = 1, FEAST_NH_DEVERR_QR_NOCONV = 2, FEAST_NH_DEVERR_TIMEOUT = 16 };
+
+/* Fault injection for tests, on the host: the next contour integration
+ * (feast_nh_filter, or the first filter of feast_nh_solve) ORs `bits` into
+ * the context's device error word after its kernels, so that the host's
+ * mapping of that word to a status (FEAST_NH_ETIMEOUT for
+ * FEAST_NH_DEVERR_TIMEOUT, ...) can be exercised without making a device
+ * wait run out or a kernel fault.  One-shot. */
+feast_nh_status feast_nh_inject_device_error(feast_nh_ctx *ctx, uint32_t bits);
 
 /* The multi-shift residual above for callers that cannot allocate device
  * memory (an application that owns all device memory through its own pool or
@@ -200,12 +236,17 @@ feast_nh_status feast_nh_multishift_residual(feast_nh_ctx *ctx, const void *X, c
  * norms, partial sums of at most 256 CTAs) that every GPU loading the library
  * holds until exit.  Limits: 1 <= m <= 128, 1 <= ne <= 64, ne*m <= 2048;
  * larger sizes, NULL blocks or bad CSR descriptors return FEAST_NH_EINVAL
- * before any device work.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress, with that device current) and caches
- * it; make that first call before any stream capture.  All calls share the
- * array: calls that overlap on the GPU (other streams, other threads) race,
- * so serialise them.  Every scratch entry a call reads is written earlier in
- * the same call, so nothing carries over between calls. */
+ * before any device work.  Runs on the CURRENT device: X, BY, R, Q, relres and
+ * the CSR arrays must live there.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current)
+ * and caches it; make that first call before any stream capture.  The
+ * quadrature nodes are formed on the device by a kernel from the contour's
+ * parameters (custom nodes are passed by value), so no host buffer is read
+ * after the call returns.  All calls share the array: calls that overlap on
+ * the GPU (other streams, other threads) race, so serialise them.  Every
+ * scratch entry a call reads is written earlier in the same call, so nothing
+ * carries over between calls.  A CUDA error left pending by earlier work of
+ * the caller is reported as FEAST_NH_ECUDA before anything is enqueued. */
 feast_nh_status feast_nh_multishift_residual_noalloc(const feast_nh_csr *A, const feast_nh_csr *B,
                                                      const feast_nh_contour *contour, const void *X,
                                                      const void *BY, void *R, void *Q, double *relres,

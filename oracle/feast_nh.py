@@ -76,20 +76,29 @@ def _BH(B, X):
     return X if B is None else B.conj().T @ X
 
 
+def _solve_each(solvers, rhs, herm):
+    """(z_j B - A)^{-1} rhs (or ^{-H}) for every node j, in node order.  A
+    solver list may instead provide solve_all(rhs, herm) returning the same
+    list (e.g. one worker process per node); the sums below are unchanged."""
+    if hasattr(solvers, "solve_all"):
+        return solvers.solve_all(rhs, herm)
+    return [s.solve(rhs, herm=herm) for s in solvers]
+
+
 def contour_integration(A, B, solvers, z, w, Y, Yh, problem="general"):
     """Step 1: Q = sum_j w_j (z_j B - A)^{-1} B Y            (eq. qr)
                Q^ = sum_j w_j^* (z_j B - A)^{-H} B^H Y^      (eq. ql)
     Complex symmetric: Q^ = conj(Q) (Sec. 2.4), valid for Y^ = conj(Y)."""
     BY = _B(B, Y)
     Q = np.zeros(Y.shape, np.complex128)
-    for j in range(len(z)):
-        Q += w[j] * solvers[j].solve(BY)
+    for j, Xj in enumerate(_solve_each(solvers, BY, False)):
+        Q += w[j] * Xj
     if problem == "complex_symmetric":
         return Q, Q.conj()
     BhYh = _BH(B, Yh)
     Qh = np.zeros(Yh.shape, np.complex128)
-    for j in range(len(z)):
-        Qh += np.conj(w[j]) * solvers[j].solve(BhYh, herm=True)
+    for j, Xj in enumerate(_solve_each(solvers, BhYh, True)):
+        Qh += np.conj(w[j]) * Xj
     return Q, Qh
 
 

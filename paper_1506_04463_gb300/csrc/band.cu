@@ -949,6 +949,51 @@ void launch_band_diag_inv(int n, int kl, int ku, int ne, const cx<T> *band, cx<T
 template void launch_band_diag_inv<float>(int, int, int, int, const cxf *, cxf *, cudaStream_t);
 size_t band_diag_inv_elems(int n, int ne) { return (size_t)ne * ceil_div(n, DIB) * 4 * DIB * DIB; }
 
+// Smallest and largest pivot modulus |u_rr| over every factor slot.  The
+// factorisation does not pivot, so a pivot that is tiny against the largest
+// one flags factors that may be inaccurate; the iterative refinement then
+// decides whether the solves still reach their tolerance.  Both values go to
+// out[0..1] as bits of non-negative doubles (atomicMin / atomicMax on them is
+// order-independent); out[0] must start at +inf bits and out[1] at 0.
+template <typename T>
+__global__ void k_band_pivot_stats(int n, int kl, int ku, int nslots, const cx<T> *__restrict__ band,
+                                   unsigned long long *out) {
+  const int W = kl + ku + 1;
+  const size_t ns = (size_t)n * W;
+  double lo = INFINITY, hi = 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * nslots;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t slot = e / n, r = e - slot * n;
+    const cx<T> u = band[slot * ns + r * W + kl];
+    const double a = hypot((double)u.re, (double)u.im);
+    const double av = (a == a) ? a : 0.0;  // NaN pivots count as zero
+    lo = fmin(lo, av);
+    hi = fmax(hi, av);
+  }
+  for (int o = 16; o; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(out, (unsigned long long)__double_as_longlong(lo));
+    atomicMax(out + 1, (unsigned long long)__double_as_longlong(hi));
+  }
+}
+__global__ void k_pivot_stats_init(unsigned long long *out) {
+  out[0] = (unsigned long long)__double_as_longlong(INFINITY);
+  out[1] = 0ull;
+}
+template <typename T>
+void launch_band_pivot_stats(int n, int kl, int ku, int nslots, const cx<T> *band, double *d_out, cudaStream_t s) {
+  unsigned long long *o = reinterpret_cast<unsigned long long *>(d_out);
+  k_pivot_stats_init<<<1, 1, 0, s>>>(o);
+  note_launch();
+  k_band_pivot_stats<T><<<grid_for((size_t)n * nslots), 256, 0, s>>>(n, kl, ku, nslots, band, o);
+  note_launch();
+}
+template void launch_band_pivot_stats<float>(int, int, int, int, const cxf *, double *, cudaStream_t);
+template void launch_band_pivot_stats<double>(int, int, int, int, const cxd *, double *, cudaStream_t);
+
 // Transposed copy of the factors for the conjugate-transpose solves: row r of
 // Bt holds column r of the factored band (lower width ku, upper width kl), so
 // that both sides read their tiles along rows.

@@ -66,6 +66,24 @@ HD cxd csqrt(cxd a) {
   return mk(fabs(a.im) / (2 * t), a.im >= 0 ? t : -t);
 }
 
+// Trapezoidal rule on a circle (kind 0) or ellipse (kind 1), Sec. 2.1 / 2.3:
+// node j (0-based) at t = pi(2j+1)/ne, z = c + e^{i phi}(a cos t + i b sin t),
+// b = ratio*a, and weight w = z'(t)/(i ne) = e^{i phi}(b cos t + i a sin t)/ne.
+// Shared by the host setup of a context and by the device-side node kernel of
+// the allocation-free entry point.
+HD void trapezoid_node(int kind, double c_re, double c_im, double a, double ratio, double phi_in, int ne, int j,
+                       cx<double> &z, cx<double> &w) {
+  const double b = a * (kind == 0 ? 1.0 : ratio);
+  const double phi = kind == 0 ? 0.0 : phi_in;
+  const double cp = cos(phi), sp = sin(phi);
+  const double th = 3.14159265358979323846 * (2.0 * j + 1.0) / ne;
+  const double ct = cos(th), st = sin(th);
+  const double xr = a * ct, xi = b * st;
+  z = mk(c_re + cp * xr - sp * xi, c_im + sp * xr + cp * xi);
+  const double wr = b * ct, wi = a * st;
+  w = mk((cp * wr - sp * wi) / ne, (sp * wr + cp * wi) / ne);
+}
+
 // CSR view of a caller-owned matrix (device pointers).  `cplx` selects
 // interleaved complex values; `conj_vals` conjugates them on read (used with
 // a transposed CSR to apply A^H).

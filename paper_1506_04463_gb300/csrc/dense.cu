@@ -701,3 +701,10 @@ void small_eig(const cxd *A, int m, cxd *lam, cxd *V, cxd *work, int *d_err, cud
   k_small_eig<<<1, 256, hsm ? hbytes : 0, s>>>(A, m, lam, V, work, d_err, hsm);
   note_launch();
 }
+
+// Host-requested device error bits (fault-injection aid): *err |= bits.
+__global__ void k_or_bits(int *err, int bits) { atomicOr(err, bits); }
+void launch_or_bits(int *d_err, int bits, cudaStream_t s) {
+  k_or_bits<<<1, 1, 0, s>>>(d_err, bits);
+  note_launch();
+}

@@ -74,6 +74,11 @@ struct feast_nh_ctx {
   double t_factor = 0, inner_res = 0;
   int inner_steps = 0;
   bool krylov_ok = true;
+  double last_inner_tol = 0;  // tolerance the last filter's inner solves aimed at
+  int n_inner_fail = 0;       // filters of the current solve that missed it
+  double *d_piv = nullptr;    // pivot statistics of the banded factors (2 doubles)
+  double piv_min = 0, piv_max = 0;
+  unsigned inject_bits = 0;   // host-requested device error bits (testing aid)
   EvPool ev_solve, ev_resid;
 };
 
@@ -127,18 +132,7 @@ void compute_nodes(const feast_nh_contour &c, std::vector<cxd> &z, std::vector<c
     }
     return;
   }
-  const double a = c.r, b = c.r * (c.kind == 0 ? 1.0 : c.ratio);
-  const double phi = c.kind == 0 ? 0.0 : c.angle;
-  const double cp = std::cos(phi), sp = std::sin(phi);
-  for (int j = 1; j <= c.ne; ++j) {
-    const double th = M_PI * (2.0 * j - 1.0) / c.ne;
-    // e^{i phi} (a cos th + i b sin th)
-    const double xr = a * std::cos(th), xi = b * std::sin(th);
-    z[j - 1] = mk(c.c_re + cp * xr - sp * xi, c.c_im + sp * xr + cp * xi);
-    // w = e^{i phi} (b cos th + i a sin th) / ne
-    const double wr = b * std::cos(th), wi = a * std::sin(th);
-    w[j - 1] = mk((cp * wr - sp * wi) / c.ne, (sp * wr + cp * wi) / c.ne);
-  }
+  for (int j = 0; j < c.ne; ++j) trapezoid_node(c.kind, c.c_re, c.c_im, c.r, c.ratio, c.angle, c.ne, j, z[j], w[j]);
 }
 
 CsrView make_view(const feast_nh_csr &M) {
@@ -220,9 +214,17 @@ void factorize(feast_nh_ctx *ctx) {
     CKC(band_factor<double>(ctx->n, ctx->klp, ctx->kup, ctx->nf, (cxd *)ctx->band, ctx->d_err, ctx->s));
   }
   CKC(cudaEventRecord(ctx->ev[5], ctx->s));
+  if (fp32(ctx))
+    launch_band_pivot_stats<float>(ctx->n, ctx->klp, ctx->kup, ctx->nf, (const cxf *)ctx->band, ctx->d_piv, ctx->s);
+  else
+    launch_band_pivot_stats<double>(ctx->n, ctx->klp, ctx->kup, ctx->nf, (const cxd *)ctx->band, ctx->d_piv, ctx->s);
   int herr = 0;
+  double piv[2] = {0, 0};
   CKC(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+  CKC(cudaMemcpyAsync(piv, ctx->d_piv, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
   CKC(cudaStreamSynchronize(ctx->s));
+  ctx->piv_min = piv[0];
+  ctx->piv_max = piv[1];
   float ms = 0;
   cudaEventElapsedTime(&ms, ctx->ev[4], ctx->ev[5]);
   ctx->t_factor = ms;
@@ -280,11 +282,21 @@ void do_filter(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, cxd *Q, cxd *Qh, 
                                          ctx->Xn,
                                          cs ? nullptr : ctx->Xhn, xns, 0, (cxd *)ctx->ysc, nullptr, ctx->s));
     ev_end(ctx, ctx->ev_solve, k);
-    launch_multishift_residual<double>(ctx->A, Bp, ne, ctx->dz, ctx->dw, ctx->Xn, BY, nullptr, Q, nullptr, m, nullptr,
-                                       ctx->s);
+    // Q = sum_j w_j X_j in the same pass that measures each shifted system's
+    // residual, so that an inaccurate direct solve is reported, not hidden
+    const int gm = launch_multishift_residual<double>(ctx->A, Bp, ne, ctx->dz, ctx->dw, ctx->Xn, BY, nullptr, Q,
+                                                      ctx->part, m, nullptr, ctx->s);
     if (!cs)
-      launch_multishift_residual<double>(ctx->AH, BHp, ne, ctx->dzc, ctx->dwc, ctx->Xhn, BhYh, nullptr, Qh, nullptr,
-                                         m, nullptr, ctx->s);
+      launch_multishift_residual<double>(ctx->AH, BHp, ne, ctx->dzc, ctx->dwc, ctx->Xhn, BhYh, nullptr, Qh,
+                                         ctx->part + (size_t)gm * ne * m, m, nullptr, ctx->s);
+    int g = launch_colnorm2(BY, m, m, n, ctx->colp, ctx->s);
+    launch_reduce_parts(ctx->colp, g, m, ctx->bynorm2, ctx->s);
+    if (!cs) {
+      g = launch_colnorm2(BhYh, m, m, n, ctx->colp, ctx->s);
+      launch_reduce_parts(ctx->colp, g, m, ctx->bynorm2 + m, ctx->s);
+    }
+    launch_residual_check(ctx->part, gm, ne, m, ctx->bynorm2, cs ? 1 : 2, inner_tol, ctx->d_maxrel, ctx->d_done,
+                          ctx->s);
     ctx->inner_steps = 1;
   } else {
     CKC(cudaMemsetAsync(ctx->d_done, 0, sizeof(int), ctx->s));
@@ -342,7 +354,37 @@ void do_filter(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, cxd *Q, cxd *Qh, 
     if (!cs) launch_node_sum(ne, ctx->dwc, ctx->Xhn, xns, n, m, Qh, ctx->s);
   }
   if (cs) launch_copy_conj(Q, Qh, (size_t)n * m, ctx->s);
+  ctx->last_inner_tol = inner_tol;
+  if (ctx->inject_bits) {
+    launch_or_bits(ctx->d_err, (int)ctx->inject_bits, ctx->s);
+    ctx->inject_bits = 0;
+  }
   check_launch(ctx, "contour integration");
+}
+
+// Status of the device error word (host copy), FEAST_NH_OK if clear.
+feast_nh_status status_from_err(feast_nh_ctx *ctx, int herr) {
+  if (herr & DEVERR_TIMEOUT) {
+    ctx->err = "a bounded wait for a tile load in the triangular solves gave up";
+    return FEAST_NH_ETIMEOUT;
+  }
+  if (herr & DEVERR_ZERO_PIVOT) {
+    ctx->err = "zero pivot in the banded factorisation of (z_j B - A): a node lies on an eigenvalue";
+    return FEAST_NH_ESINGULAR;
+  }
+  if (herr & DEVERR_QR_NOCONV) {
+    ctx->err = "small dense eigenproblem (B_Q or reduced): QR iteration did not converge";
+    return FEAST_NH_ECUDA;
+  }
+  return FEAST_NH_OK;
+}
+
+// Whether the last filter's shifted solves stopped above their tolerance
+// (largest relative residual in h_small[0] after read_status / read_inner).
+bool inner_missed(const feast_nh_ctx *ctx) {
+  if (krylov(ctx)) return !ctx->krylov_ok;
+  const double r = ctx->h_small[0];
+  return !(r <= ctx->last_inner_tol);
 }
 
 RRParams rr_params(const feast_nh_ctx *ctx) {
@@ -670,6 +712,7 @@ feast_nh_status feast_nh_init(feast_nh_ctx **out, const feast_nh_csr *A, const f
     ctx->d_done = dalloc<int>(ctx, sizeof(int));
     ctx->d_err = dalloc<int>(ctx, sizeof(int));
     ctx->d_maxrel = dalloc<double>(ctx, sizeof(double));
+    ctx->d_piv = dalloc<double>(ctx, 2 * sizeof(double));
     CKC(cudaMemsetAsync(ctx->d_maxrel, 0, sizeof(double), ctx->s));
     const size_t sm = (size_t)kMaxM0 * kMaxM0 * sizeof(cxd);
     ctx->BQ = dalloc<cxd>(ctx, sm);
@@ -727,8 +770,26 @@ feast_nh_status feast_nh_filter(feast_nh_ctx *ctx, const void *Y, const void *Yh
     REQ(cs_mode(ctx) || Yh, "filter: Yh is required unless the problem is complex symmetric");
     CKC(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->s));
     do_filter(ctx, (const cxd *)Y, (const cxd *)Yh, (cxd *)Q, (cxd *)Qh, m);
-    if (krylov(ctx) && !ctx->krylov_ok) {
-      ctx->err = "BiCGStab stopped at inner_max iterations above inner_tol (outputs hold the last iterate)";
+    // the filter's status: device error word and the largest relative
+    // residual of the shifted solves (one small read)
+    CKC(cudaMemcpyAsync(ctx->h_small, ctx->d_maxrel, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+    CKC(cudaMemcpyAsync(ctx->h_small + 1, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+    CKC(cudaStreamSynchronize(ctx->s));
+    int herr = 0;
+    std::memcpy(&herr, ctx->h_small + 1, sizeof(int));
+    const feast_nh_status es = status_from_err(ctx, herr);
+    if (es != FEAST_NH_OK) return es;
+    if (!krylov(ctx)) ctx->inner_res = ctx->h_small[0];
+    if (inner_missed(ctx)) {
+      char msg[200];
+      if (krylov(ctx))
+        std::snprintf(msg, sizeof msg, "BiCGStab stopped at inner_max iterations above inner_tol (largest relative "
+                                       "residual %.3g; outputs hold the last iterate)", ctx->inner_res);
+      else
+        std::snprintf(msg, sizeof msg, "the refined shifted solves stopped at inner_max steps above inner_tol "
+                                       "(largest relative residual %.3g; outputs hold the last iterate)",
+                      ctx->inner_res);
+      ctx->err = msg;
       return FEAST_NH_EINNER;
     }
   } catch (const Fail &f) {
@@ -758,17 +819,13 @@ feast_nh_status feast_nh_rr(feast_nh_ctx *ctx, const void *Q, const void *Qh, in
       info->kl = ctx->kl;
       info->ku = ctx->ku;
       info->n_factorizations = krylov(ctx) ? 0 : ctx->nf;
+      info->pivot_min = ctx->piv_min;
+      info->pivot_max = ctx->piv_max;
     }
     int herr = 0;
     std::memcpy(&herr, ctx->h_small + 1, sizeof(int));
-    if (herr & DEVERR_TIMEOUT) {
-      ctx->err = "a bounded wait for a tile load in the triangular solves gave up";
-      return FEAST_NH_ETIMEOUT;
-    }
-    if (herr & DEVERR_QR_NOCONV) {
-      ctx->err = "small dense eigenproblem (B_Q or reduced): QR iteration did not converge";
-      return FEAST_NH_ECUDA;
-    }
+    const feast_nh_status es = status_from_err(ctx, herr);
+    if (es != FEAST_NH_OK) return es;
   } catch (const Fail &f) {
     return f.st;
   }
@@ -788,6 +845,7 @@ feast_nh_status feast_nh_solve(feast_nh_ctx *ctx, const void *Y0, const void *Yh
     CKC(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s));
     ctx->factored = false;  // each solve factorises afresh and keeps the factors for its iterations
     ctx->have_prev = 0;
+    ctx->n_inner_fail = 0;
     ev_harvest(ctx->ev_solve);
     ev_harvest(ctx->ev_resid);
     ctx->ev_solve.ms = ctx->ev_resid.ms = 0;
@@ -821,15 +879,10 @@ feast_nh_status feast_nh_solve(feast_nh_ctx *ctx, const void *Y0, const void *Yh
       t_rr += b;
       int herr = 0;
       std::memcpy(&herr, ctx->h_small + 1, sizeof(int));
-      if (herr & DEVERR_TIMEOUT) {
-        ctx->err = "a bounded wait for a tile load in the triangular solves gave up";
-        throw Fail{FEAST_NH_ETIMEOUT};
-      }
-      if (herr & DEVERR_QR_NOCONV) {
-        ctx->err = "small dense eigenproblem (B_Q or reduced): QR iteration did not converge";
-        throw Fail{FEAST_NH_ECUDA};
-      }
-      ctx->inner_res = ctx->h_small[0];
+      const feast_nh_status es = status_from_err(ctx, herr);
+      if (es != FEAST_NH_OK) throw Fail{es};
+      if (!krylov(ctx)) ctx->inner_res = ctx->h_small[0];
+      if (inner_missed(ctx)) ++ctx->n_inner_fail;
       conv = ctx->h_st->conv != 0;
       if (conv) break;
       m = mt;
@@ -874,10 +927,23 @@ feast_nh_status feast_nh_solve(feast_nh_ctx *ctx, const void *Y0, const void *Yh
       info->n_solve_launches = ctx->ev_solve.launches;
       info->n_resid_launches = ctx->ev_resid.launches;
       info->n_factorizations = krylov(ctx) ? 0 : ctx->nf;
+      info->inner_fail = ctx->n_inner_fail;
+      info->pivot_min = ctx->piv_min;
+      info->pivot_max = ctx->piv_max;
     }
     if (!conv) {
-      ctx->err = "no convergence within max_iter outer iterations";
-      ret = FEAST_NH_ENOCONV;
+      if (ctx->n_inner_fail > 0) {
+        char msg[200];
+        std::snprintf(msg, sizeof msg,
+                      "no convergence within max_iter outer iterations; the shifted solves of %d filter(s) stopped "
+                      "above their tolerance (largest relative residual %.3g)",
+                      ctx->n_inner_fail, ctx->inner_res);
+        ctx->err = msg;
+        ret = FEAST_NH_EINNER;
+      } else {
+        ctx->err = "no convergence within max_iter outer iterations";
+        ret = FEAST_NH_ENOCONV;
+      }
     }
   } catch (const Fail &f) {
     return f.st;
@@ -887,14 +953,43 @@ feast_nh_status feast_nh_solve(feast_nh_ctx *ctx, const void *Y0, const void *Yh
 
 uint64_t feast_nh_kernel_launches(void) { return g_launches.load(); }
 
+feast_nh_status feast_nh_small_eig(feast_nh_ctx *ctx, const void *M, int32_t m, void *lambda, void *V) {
+  if (!ctx) return FEAST_NH_EINVAL;
+  try {
+    REQ(M && lambda && V && m >= 1 && m <= kMaxM0, "small_eig: bad arguments (1 <= m <= 128)");
+    CKC(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->s));
+    small_eig((const cxd *)M, m, (cxd *)lambda, (cxd *)V, ctx->swork, ctx->d_err, ctx->s);
+    check_launch(ctx, "small_eig");
+    CKC(cudaMemcpyAsync(ctx->h_small + 1, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+    CKC(cudaStreamSynchronize(ctx->s));
+    int herr = 0;
+    std::memcpy(&herr, ctx->h_small + 1, sizeof(int));
+    const feast_nh_status es = status_from_err(ctx, herr);
+    if (es != FEAST_NH_OK) return es;
+  } catch (const Fail &f) {
+    return f.st;
+  }
+  return FEAST_NH_OK;
+}
+
+feast_nh_status feast_nh_inject_device_error(feast_nh_ctx *ctx, uint32_t bits) {
+  if (!ctx) return FEAST_NH_EINVAL;
+  ctx->inject_bits |= bits;
+  return FEAST_NH_OK;
+}
+
 feast_nh_status feast_nh_multishift_residual(feast_nh_ctx *ctx, const void *X, const void *BY, void *R, void *Q,
-                                             int32_t m) {
+                                             int32_t m, int32_t r_single) {
   if (!ctx) return FEAST_NH_EINVAL;
   try {
     REQ(X && BY && R && m >= 1 && m <= ctx->m0, "multishift_residual: bad arguments");
-    launch_multishift_residual<double>(ctx->A, ctx->hasB ? &ctx->B : nullptr, ctx->ne, ctx->dz, ctx->dw,
-                                       (const cxd *)X, (const cxd *)BY, (cxd *)R, (cxd *)Q, nullptr, m, nullptr,
-                                       ctx->s);
+    const CsrView *Bp = ctx->hasB ? &ctx->B : nullptr;
+    if (r_single)
+      launch_multishift_residual<float>(ctx->A, Bp, ctx->ne, ctx->dz, ctx->dw, (const cxd *)X, (const cxd *)BY,
+                                        (cxf *)R, (cxd *)Q, nullptr, m, nullptr, ctx->s);
+    else
+      launch_multishift_residual<double>(ctx->A, Bp, ctx->ne, ctx->dz, ctx->dw, (const cxd *)X, (const cxd *)BY,
+                                         (cxd *)R, (cxd *)Q, nullptr, m, nullptr, ctx->s);
     check_launch(ctx, "multishift_residual");
   } catch (const Fail &f) {
     return f.st;

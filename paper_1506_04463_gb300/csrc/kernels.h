@@ -37,6 +37,9 @@ template <typename T> size_t band_solve_scratch_elems(int n, int m, int ne);
 template <typename T>
 void launch_band_diag_inv(int n, int kl, int ku, int ne, const cx<T> *band, cx<T> *dinv, cudaStream_t s);
 size_t band_diag_inv_elems(int n, int ne);
+// Smallest / largest pivot modulus over all factor slots -> d_out[0], d_out[1].
+template <typename T>
+void launch_band_pivot_stats(int n, int kl, int ku, int nslots, const cx<T> *band, double *d_out, cudaStream_t s);
 template <typename T> bool band_fits(int kl, int ku);
 template <typename T> bool band_solve_fits(int kl, int ku);
 
@@ -91,6 +94,9 @@ void block_times_small(const cxd *X, int ldx, int mx, const cxd *S, int lds, int
 int launch_colnorm2(const cxd *X, int ld, int m, int n, double *partial, cudaStream_t s);
 void launch_copy_conj(const cxd *X, cxd *Y, size_t count, cudaStream_t s);
 void launch_broadcast_block(const cxd *X, cxd *Y, size_t count, int copies, cudaStream_t s);
+
+// *d_err |= bits (host-side fault injection through the device error word).
+void launch_or_bits(int *d_err, int bits, cudaStream_t s);
 
 // Small single-CTA work on m x m matrices in global memory (row-major).
 void small_eig(const cxd *A, int m, cxd *lam, cxd *V, cxd *work, int *d_err, cudaStream_t s);

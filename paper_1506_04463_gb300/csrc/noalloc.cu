@@ -12,7 +12,6 @@
 // library holds until the process exits.
 #include <cmath>
 #include <mutex>
-#include <vector>
 
 #include "feast_nh.h"
 #include "kernels.h"
@@ -35,6 +34,31 @@ static __device__ __align__(256) double g_noalloc_scratch[kNaDoubles];
 std::mutex g_na_mutex;
 double *g_na_ptr[64] = {};  // device address of g_noalloc_scratch, per device
 
+// Contour passed to the node kernel by value: the parameters of a circle or
+// ellipse, or (kind 2) the caller's nodes and weights themselves (2 KiB at
+// most), so that no host buffer has to outlive the call.
+struct NaContour {
+  int kind, ne;
+  double c_re, c_im, r, ratio, angle;
+  cxd z[kMaxNe], w[kMaxNe];
+};
+
+// zw[0..ne) = nodes, zw[ne..2ne) = weights (trapezoidal rule of Sec. 2.3 for
+// kinds 0/1, the caller's values for kind 2).
+__global__ void k_na_nodes(NaContour c, cxd *zw) {
+  const int j = threadIdx.x;
+  if (j >= c.ne) return;
+  cxd z, w;
+  if (c.kind == 2) {
+    z = c.z[j];
+    w = c.w[j];
+  } else {
+    trapezoid_node(c.kind, c.c_re, c.c_im, c.r, c.ratio, c.angle, c.ne, j, z, w);
+  }
+  zw[j] = z;
+  zw[c.ne + j] = w;
+}
+
 __global__ void k_na_relres(const double *partial, int nparts, int P, int m, const double *bynorm2, double *relres) {
   const int pair = blockIdx.x * blockDim.x + threadIdx.x;
   if (pair >= P) return;
@@ -42,30 +66,6 @@ __global__ void k_na_relres(const double *partial, int nparts, int P, int m, con
   for (int p = 0; p < nparts; ++p) s += partial[(size_t)p * P + pair];
   const double d = bynorm2[pair % m];
   relres[pair] = d > 0 ? sqrt(s / d) : sqrt(s);
-}
-
-void na_nodes(const feast_nh_contour &c, std::vector<double> &zw) {
-  // trapezoidal rule of Sec. 2.3 (same definition as feast_nh_nodes)
-  zw.assign(4 * c.ne, 0.0);
-  if (c.kind == 2) {
-    for (int j = 0; j < 2 * c.ne; ++j) {
-      zw[j] = c.z[j];
-      zw[2 * c.ne + j] = c.w[j];
-    }
-    return;
-  }
-  const double a = c.r, b = c.r * (c.kind == 0 ? 1.0 : c.ratio);
-  const double phi = c.kind == 0 ? 0.0 : c.angle;
-  const double cp = std::cos(phi), sp = std::sin(phi);
-  for (int j = 1; j <= c.ne; ++j) {
-    const double th = M_PI * (2.0 * j - 1.0) / c.ne;
-    const double xr = a * std::cos(th), xi = b * std::sin(th);
-    zw[2 * (j - 1)] = c.c_re + cp * xr - sp * xi;
-    zw[2 * (j - 1) + 1] = c.c_im + sp * xr + cp * xi;
-    const double wr = b * std::cos(th), wi = a * std::sin(th);
-    zw[2 * c.ne + 2 * (j - 1)] = (cp * wr - sp * wi) / c.ne;
-    zw[2 * c.ne + 2 * (j - 1) + 1] = (sp * wr + cp * wi) / c.ne;
-  }
 }
 
 CsrView na_view(const feast_nh_csr &M) {
@@ -92,9 +92,13 @@ extern "C" feast_nh_status feast_nh_multishift_residual_noalloc(const feast_nh_c
             (B->dtype != FEAST_NH_R64 && B->dtype != FEAST_NH_C64)))
     return FEAST_NH_EINVAL;
   if (!contour || contour->ne < 1 || contour->ne > kMaxNe || contour->kind < 0 || contour->kind > 2 ||
-      (contour->kind == 2 && (!contour->z || !contour->w)))
+      (contour->kind == 2 && (!contour->z || !contour->w)) || (contour->kind != 2 && !(contour->r > 0)) ||
+      (contour->kind == 1 && !(contour->ratio > 0)))
     return FEAST_NH_EINVAL;
   if (!X || !BY || !R || !relres || m < 1 || m > kMaxM0 || contour->ne * m > kNaMaxPairs) return FEAST_NH_EINVAL;
+  // an error left pending by the caller's earlier work is not this call's:
+  // report it before enqueuing anything, so that later checks see only ours
+  if (cudaGetLastError() != cudaSuccess) return FEAST_NH_ECUDA;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return FEAST_NH_ECUDA;
@@ -110,14 +114,25 @@ extern "C" feast_nh_status feast_nh_multishift_residual_noalloc(const feast_nh_c
     }
     base = g_na_ptr[dev];
   }
-  std::vector<double> zw;
-  na_nodes(*contour, zw);
   const int ne = contour->ne;
-  if (cudaMemcpyAsync(base + kNaOffNodes, zw.data(), zw.size() * sizeof(double), cudaMemcpyHostToDevice, s) !=
-      cudaSuccess)
-    return FEAST_NH_ECUDA;
-  const cxd *dz = reinterpret_cast<const cxd *>(base + kNaOffNodes);
+  NaContour nc{};
+  nc.kind = contour->kind;
+  nc.ne = ne;
+  nc.c_re = contour->c_re;
+  nc.c_im = contour->c_im;
+  nc.r = contour->r;
+  nc.ratio = contour->ratio;
+  nc.angle = contour->angle;
+  if (contour->kind == 2)
+    for (int j = 0; j < ne; ++j) {
+      nc.z[j] = mk(contour->z[2 * j], contour->z[2 * j + 1]);
+      nc.w[j] = mk(contour->w[2 * j], contour->w[2 * j + 1]);
+    }
+  cxd *dz = reinterpret_cast<cxd *>(base + kNaOffNodes);
   const cxd *dw = dz + ne;
+  k_na_nodes<<<1, kMaxNe, 0, s>>>(nc, dz);
+  note_launch();
+  if (cudaGetLastError() != cudaSuccess) return FEAST_NH_ECUDA;
   const CsrView Av = na_view(*A);
   CsrView Bv;
   if (B) Bv = na_view(*B);
@@ -125,9 +140,11 @@ extern "C" feast_nh_status feast_nh_multishift_residual_noalloc(const feast_nh_c
   // ||(BY)_c||^2: every partial slot used is rewritten by this call
   const int gc = launch_colnorm2((const cxd *)BY, m, m, n, base + kNaOffCol, s);
   launch_reduce_parts(base + kNaOffCol, gc, m, base + kNaOffBy, s);
+  if (cudaGetLastError() != cudaSuccess) return FEAST_NH_ECUDA;
   const int gm = launch_multishift_residual_capped<double>(Av, B ? &Bv : nullptr, ne, dz, dw, (const cxd *)X,
                                                            (const cxd *)BY, (cxd *)R, (cxd *)Q, base + kNaOffPart,
                                                            m, kNaMaxGrid, s);
+  if (cudaGetLastError() != cudaSuccess) return FEAST_NH_ECUDA;
   const int P = ne * m;
   k_na_relres<<<ceil_div(P, 128), 128, 0, s>>>(base + kNaOffPart, gm, P, m, base + kNaOffBy, relres);
   note_launch();

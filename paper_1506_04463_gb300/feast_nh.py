@@ -16,6 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfeast_nh.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EINNER, ESINGULAR, ETIMEOUT = range(8)
+DEVERR_ZERO_PIVOT, DEVERR_QR_NOCONV, DEVERR_TIMEOUT = 1, 2, 16
 R64, C64 = 0, 1
 INNER_BANDED, INNER_BICGSTAB = 0, 1
 PREC_FP64, PREC_FP32_IR = 0, 1
@@ -45,7 +46,8 @@ class Info(C.Structure):
                 ("ku", C.c_int32), ("max_res", C.c_double), ("inner_res", C.c_double),
                 ("t_factor_ms", C.c_double), ("t_filter_ms", C.c_double), ("t_rr_ms", C.c_double),
                 ("t_total_ms", C.c_double), ("t_solve_kernel_ms", C.c_double), ("t_resid_kernel_ms", C.c_double),
-                ("n_solve_launches", C.c_int32), ("n_resid_launches", C.c_int32), ("n_factorizations", C.c_int32)]
+                ("n_solve_launches", C.c_int32), ("n_resid_launches", C.c_int32), ("n_factorizations", C.c_int32),
+                ("inner_fail", C.c_int32), ("pivot_min", C.c_double), ("pivot_max", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -53,7 +55,8 @@ class Info(C.Structure):
 
 EXPORTS = ["feast_nh_default_opts", "feast_nh_init", "feast_nh_filter", "feast_nh_rr", "feast_nh_solve",
            "feast_nh_destroy", "feast_nh_strerror", "feast_nh_last_error", "feast_nh_nodes",
-           "feast_nh_multishift_residual", "feast_nh_kernel_launches", "feast_nh_multishift_residual_noalloc"]
+           "feast_nh_multishift_residual", "feast_nh_kernel_launches", "feast_nh_multishift_residual_noalloc",
+           "feast_nh_small_eig", "feast_nh_inject_device_error"]
 
 _lib = None
 
@@ -81,14 +84,16 @@ def lib():
     L.feast_nh_last_error.argtypes = [vp]
     L.feast_nh_last_error.restype = C.c_char_p
     L.feast_nh_nodes.argtypes = [C.POINTER(ContourS), C.POINTER(C.c_double), C.POINTER(C.c_double)]
-    L.feast_nh_multishift_residual.argtypes = [vp, vp, vp, vp, vp, i32]
+    L.feast_nh_multishift_residual.argtypes = [vp, vp, vp, vp, vp, i32, i32]
+    L.feast_nh_small_eig.argtypes = [vp, vp, i32, vp, vp]
+    L.feast_nh_inject_device_error.argtypes = [vp, C.c_uint32]
     L.feast_nh_multishift_residual_noalloc.argtypes = [C.POINTER(Csr), C.POINTER(Csr), C.POINTER(ContourS), vp, vp,
                                                        vp, vp, vp, i32, vp]
     L.feast_nh_multishift_residual_noalloc.restype = i32
     L.feast_nh_kernel_launches.argtypes = []
     L.feast_nh_kernel_launches.restype = C.c_uint64
     for f in ("feast_nh_init", "feast_nh_filter", "feast_nh_rr", "feast_nh_solve", "feast_nh_nodes",
-              "feast_nh_multishift_residual"):
+              "feast_nh_multishift_residual", "feast_nh_small_eig", "feast_nh_inject_device_error"):
         getattr(L, f).restype = i32
     _lib = L
     return L
@@ -135,20 +140,44 @@ def kernel_launches() -> int:
 def multishift_residual_noalloc(A_dev, B_dev, contour, X, BY, want_q=True, stream=None):
     """feast_nh_multishift_residual_noalloc: R, Q and relative column norms
     with no context and no device allocation inside the library (the output
-    tensors are allocated here by the caller)."""
+    tensors are allocated here by the caller).
+
+    X: (ne, n, m) and BY: (n, m), contiguous complex128 on the device that
+    holds the CSR arrays; the call runs with that device current, on `stream`
+    (default: its current stream)."""
+    if X.dtype != torch.complex128 or BY.dtype != torch.complex128:
+        raise TypeError("X and BY must be complex128")
+    if X.dim() != 3 or BY.dim() != 2:
+        raise ValueError("X must be (ne, n, m) and BY (n, m)")
+    if not (X.is_contiguous() and BY.is_contiguous()):
+        raise ValueError("X and BY must be contiguous (the kernels read them after this call returns)")
     ne, n, m = X.shape
-    R = torch.empty_like(X)
-    Q = torch.empty((n, m), dtype=torch.complex128, device=X.device) if want_q else None
-    rel = torch.empty(ne * m, dtype=torch.float64, device=X.device)
     cs, keep = contour_struct(contour)
-    a = _csr_struct(A_dev)
-    b = _csr_struct(B_dev) if B_dev is not None else None
-    st = stream if stream is not None else torch.cuda.current_stream(X.device)
-    rc = lib().feast_nh_multishift_residual_noalloc(C.byref(a), C.byref(b) if b is not None else None, C.byref(cs),
-                                                    _ptr(X.contiguous()), _ptr(BY.contiguous()), _ptr(R), _ptr(Q),
-                                                    _ptr(rel), m, C.c_void_p(st.cuda_stream))
-    if rc != OK:
-        raise FeastError(rc, "feast_nh_multishift_residual_noalloc")
+    if ne != cs.ne or BY.shape != (n, m) or n != A_dev[4] or (B_dev is not None and B_dev[4] != n):
+        raise ValueError(f"shape mismatch: X {tuple(X.shape)}, BY {tuple(BY.shape)}, n={A_dev[4]}, ne={cs.ne}")
+    devs = {X.device, BY.device, A_dev[0].device, A_dev[2].device}
+    if B_dev is not None:
+        devs |= {B_dev[0].device, B_dev[2].device}
+    if len(devs) != 1 or X.device.type != "cuda":
+        raise ValueError("all operands must be on the same CUDA device")
+    with torch.cuda.device(X.device):
+        R = torch.empty_like(X)
+        Q = torch.empty((n, m), dtype=torch.complex128, device=X.device) if want_q else None
+        rel = torch.empty(ne * m, dtype=torch.float64, device=X.device)
+        a = _csr_struct(A_dev)
+        b = _csr_struct(B_dev) if B_dev is not None else None
+        st = stream if stream is not None else torch.cuda.current_stream(X.device)
+        rc = lib().feast_nh_multishift_residual_noalloc(C.byref(a), C.byref(b) if b is not None else None,
+                                                        C.byref(cs), _ptr(X), _ptr(BY), _ptr(R), _ptr(Q), _ptr(rel),
+                                                        m, C.c_void_p(st.cuda_stream))
+        if rc != OK:
+            raise FeastError(rc, "feast_nh_multishift_residual_noalloc")
+        if st != torch.cuda.current_stream(X.device):
+            # the caching allocator must not hand these blocks out again before
+            # the kernels on `st` have used them
+            for t in (X, BY, R, Q, rel):
+                if t is not None:
+                    t.record_stream(st)
     return R, Q, rel.view(ne, m)
 
 
@@ -210,8 +239,8 @@ class FeastNH:
             raise FeastError(st, "feast_nh_init (see argument checks)")
         self.h = h
 
-    def _check(self, st, what):
-        if st not in (OK, ENOCONV):
+    def _check(self, st, what, ok=(OK, ENOCONV)):
+        if st not in ok:
             raise FeastError(st, f"{what}: {lib().feast_nh_last_error(self.h).decode()}")
         return st
 
@@ -249,18 +278,38 @@ class FeastNH:
         info = Info()
         st = lib().feast_nh_solve(self.h, _ptr(Y0.contiguous()), _ptr(None if Yh0 is None else Yh0.contiguous()),
                                   _ptr(lam), _ptr(X), _ptr(Xh), _ptr(res), C.byref(mf), C.byref(info))
-        self._check(st, "feast_nh_solve")
+        # ENOCONV / EINNER: the outputs hold the best iterate, the status says why
+        self._check(st, "feast_nh_solve", ok=(OK, ENOCONV, EINNER))
         m = mf.value
         return dict(status=st, lam=lam[:m], X=X[:, :m], Xh=Xh[:, :m], res=res[:m], m=m, info=info.as_dict())
 
-    def multishift_residual(self, X, BY, want_q=True):
+    def multishift_residual(self, X, BY, want_q=True, r_single=False):
         ne, n, m = X.shape
-        R = torch.empty_like(X)
+        R = torch.empty(X.shape, dtype=torch.complex64 if r_single else torch.complex128, device=X.device)
         Q = self._blk(m) if want_q else None
-        st = lib().feast_nh_multishift_residual(self.h, _ptr(X.contiguous()), _ptr(BY.contiguous()), _ptr(R),
-                                                _ptr(Q), m)
+        Xc, BYc = X.contiguous(), BY.contiguous()
+        st = lib().feast_nh_multishift_residual(self.h, _ptr(Xc), _ptr(BYc), _ptr(R), _ptr(Q), m,
+                                                1 if r_single else 0)
         self._check(st, "feast_nh_multishift_residual")
+        self.stream.synchronize()
         return R, Q
+
+    def small_eig(self, M):
+        """Eigenvalues and right eigenvectors of an m x m complex matrix by the
+        library's small dense eigensolver (device tensors)."""
+        m = M.shape[0]
+        Mc = M.to(torch.complex128).contiguous()
+        lam = torch.empty(m, dtype=torch.complex128, device=M.device)
+        V = torch.empty((m, m), dtype=torch.complex128, device=M.device)
+        st = lib().feast_nh_small_eig(self.h, _ptr(Mc), m, _ptr(lam), _ptr(V))
+        self._check(st, "feast_nh_small_eig")
+        return lam, V
+
+    def inject_device_error(self, bits):
+        """Host-side fault injection: the next filter ORs `bits` into the
+        device error word (no device fault is made)."""
+        st = lib().feast_nh_inject_device_error(self.h, int(bits))
+        self._check(st, "feast_nh_inject_device_error")
 
     def close(self):
         if getattr(self, "h", None):

@@ -83,3 +83,9 @@ def test_shifted_residual_definition():
     R, Q = shifted_residuals(A, None, np.array([1j, 2.0]), np.array([0.5, 0.25]), X, np.zeros((3, 1)))
     assert np.allclose(R[0, :, 0], -(1j - np.array([1, 2, 3])))
     assert np.allclose(Q, 0.75)
+
+
+def test_new_entry_points_reject_null_context(L):
+    assert L.feast_nh_small_eig(None, None, 4, None, None) == F.EINVAL
+    assert L.feast_nh_inject_device_error(None, F.DEVERR_TIMEOUT) == F.EINVAL
+    assert L.feast_nh_multishift_residual(None, None, None, None, None, 4, 0) == F.EINVAL
