@@ -97,6 +97,8 @@ typedef struct {
   int32_t problem;    /* FEAST_NH_PROBLEM_GENERAL */
   int32_t timing;     /* 1: record CUDA events around the banded solve and
                          multi-shift kernels; totals go to feast_nh_info   */
+  int32_t krylov_max; /* 1000: Krylov iterations per refinement step of the
+                         batched solver (feast_nh_batch_*)                  */
 } feast_nh_opts;
 
 /* Per-call record (host).  Times are CUDA-event milliseconds on the stream. */
@@ -199,6 +201,14 @@ feast_nh_status feast_nh_nodes(const feast_nh_contour *contour, double *z, doubl
 feast_nh_status feast_nh_multishift_residual(feast_nh_ctx *ctx, const void *X, const void *BY, void *R,
                                              void *Q, int32_t m, int32_t r_single);
 
+/* The single-precision multi-shift operator of the Krylov sweeps (eq. qr /
+ * eq. ql operators for every node at once): side 0: V_j = (z_j B - A) P_j,
+ * side 1: V_j = (conj(z_j) B^H - A^H) P_j, for every node j and column c in
+ * one pass over the CSR arrays.  P, V: ne node-major blocks of n x m
+ * row-major complex FLOAT (interleaved), device, owned by the caller;
+ * FP32 arithmetic.  Asynchronous on ctx's stream. */
+feast_nh_status feast_nh_multishift_spmm(feast_nh_ctx *ctx, const void *P, void *V, int32_t m, int32_t side);
+
 /* Eigen-decomposition of an m x m complex matrix M (device, row-major,
  * 1 <= m <= 128) by the library's small dense eigensolver, the one used for
  * B_Q = V Gamma V^^H (eq. bdiag, Sec. 2.5) and the reduced problem of step
@@ -251,6 +261,63 @@ feast_nh_status feast_nh_multishift_residual_noalloc(const feast_nh_csr *A, cons
                                                      const feast_nh_contour *contour, const void *X,
                                                      const void *BY, void *R, void *Q, double *relres,
                                                      int32_t m, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Many independent problems in one solve (the independence of contours and
+ * of quadrature nodes, Sec. 4.1).  Problem p is the standard problem
+ * (B = I) of its own CSR matrix A[p] (device, 0-based LOCAL column indices,
+ * order n_p >= m0) on its own contour contours[p] (kinds 0, 1 or 2; the same
+ * ne <= 16 for all).  The contour integration of every problem, node and
+ * column runs in ONE persistent cooperative launch: shifted systems solved
+ * by Jacobi-preconditioned BiCGStab inside iterative refinement (opts.
+ * precision FP32_IR: single-precision Krylov sweeps, FP64 residuals and
+ * updates; FP64: all in double), Q = sum_j w_j X_j per problem.  The
+ * Rayleigh-Ritz step of each problem (Fig. alg:three steps 2-5) then runs
+ * on that problem's own stream, all problems concurrently.  Converged
+ * problems drop out; the others continue.  The launch shape (threads per
+ * CTA, CTAs per SM, rows per tile) is chosen at init by timing candidates.
+ *
+ * Blocks are DEVICE complex double, rows of all problems concatenated in
+ * problem order: problem p's rows start at off_p = n_0 + ... + n_{p-1}, and
+ * its n_p x m0 row-major block starts at element off_p * m0 (so Y0 is a
+ * C-contiguous (sum n_p, m0) array).  opts.inner_kind must be
+ * FEAST_NH_INNER_BICGSTAB, opts.problem GENERAL; inner_tol, inner_max and
+ * krylov_max bound the refinement and the Krylov iterations. */
+typedef struct feast_nh_batch feast_nh_batch; /* opaque */
+
+typedef struct {
+  int32_t iterations;          /* outer iterations (the slowest problem)      */
+  int32_t converged_problems;  /* problems whose test of step 5 passed        */
+  int32_t inner_fail;          /* filters with a system above its tolerance   */
+  int32_t krylov_iterations;   /* summed over filters, sides and refinements  */
+  int32_t refine_steps;        /* summed over filters and sides               */
+  int32_t threads, tile_rows, grid; /* launch shape the tuner chose          */
+  double max_res;              /* largest eq. (res) residual returned         */
+  double inner_res;            /* largest relative inner residual, last filter */
+  double t_filter_ms, t_rr_ms, t_total_ms, t_autotune_ms;
+} feast_nh_batch_info;
+
+/* Creates the batch: per-problem transposed CSR (for the ^H solves),
+ * quadrature nodes, workspace; runs the launch-shape tuner (a few short
+ * launches on a fixed input).  Enqueued on `stream`; waits for it. */
+feast_nh_status feast_nh_batch_init(feast_nh_batch **batch, int32_t nprob, const feast_nh_csr *A,
+                                    const feast_nh_contour *contours, int32_t m0, const feast_nh_opts *opts,
+                                    void *stream);
+
+/* Solves every problem from start blocks Y0, Yh0 ((sum n_p) x m0).  Outputs
+ * per problem p: m_found[p] (host) converged pairs inside its contour, first
+ * in X, Xh (problem p's block at element off_p * m0, leading dimension m0),
+ * lambda[p*m0 + k] (device, complex) and res[p*m0 + k] (device, eq. res),
+ * normalised as for feast_nh_solve; iterations[p] (host, may be NULL) the
+ * outer iterations problem p took.  Returns FEAST_NH_ENOCONV (or
+ * FEAST_NH_EINNER if inner solves also missed) when some problem did not
+ * converge within opts.max_iter. */
+feast_nh_status feast_nh_batch_solve(feast_nh_batch *batch, const void *Y0, const void *Yh0, double *lambda,
+                                     void *X, void *Xh, double *res, int32_t *m_found, int32_t *iterations,
+                                     feast_nh_batch_info *info);
+
+void feast_nh_batch_destroy(feast_nh_batch *batch);
+const char *feast_nh_batch_last_error(const feast_nh_batch *batch);
 
 #ifdef __cplusplus
 }

@@ -2,7 +2,9 @@
 // Rayleigh-Ritz and the outer loop of Fig. alg:three.  Host code here only
 // sizes, sequences and checks device work; every numerical step runs in the
 // kernels of band.cu, spmm.cu, dense.cu and rr.cu.
+#include <algorithm>
 #include <atomic>
+#include <thread>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -79,6 +81,8 @@ struct feast_nh_ctx {
   double *d_piv = nullptr;    // pivot statistics of the banded factors (2 doubles)
   double piv_min = 0, piv_max = 0;
   unsigned inject_bits = 0;   // host-requested device error bits (testing aid)
+  bool rr_only = false;       // Rayleigh-Ritz workspace only (one problem of a batch)
+  bool own_stream = false;
   EvPool ev_solve, ev_resid;
 };
 
@@ -275,43 +279,36 @@ void do_filter(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, cxd *Q, cxd *Qh, 
     ctx->inner_steps = it_r > it_l ? it_r : it_l;
     ctx->inner_res = rel_r > rel_l ? rel_r : rel_l;
     ctx->krylov_ok = !(ctx->inner_res > inner_tol);
-  } else if (!fp32(ctx)) {
-    int k = ev_begin(ctx, ctx->ev_solve);
-    CKC(band_solve_sides<double, double>(n, ctx->klp, ctx->kup, ne, ctx->fmap.data(), (const cxd *)ctx->band, nullptr,
-                                         BY, BhYh, 0, m,
-                                         ctx->Xn,
-                                         cs ? nullptr : ctx->Xhn, xns, 0, (cxd *)ctx->ysc, nullptr, ctx->s));
-    ev_end(ctx, ctx->ev_solve, k);
-    // Q = sum_j w_j X_j in the same pass that measures each shifted system's
-    // residual, so that an inaccurate direct solve is reported, not hidden
-    const int gm = launch_multishift_residual<double>(ctx->A, Bp, ne, ctx->dz, ctx->dw, ctx->Xn, BY, nullptr, Q,
-                                                      ctx->part, m, nullptr, ctx->s);
-    if (!cs)
-      launch_multishift_residual<double>(ctx->AH, BHp, ne, ctx->dzc, ctx->dwc, ctx->Xhn, BhYh, nullptr, Qh,
-                                         ctx->part + (size_t)gm * ne * m, m, nullptr, ctx->s);
-    int g = launch_colnorm2(BY, m, m, n, ctx->colp, ctx->s);
-    launch_reduce_parts(ctx->colp, g, m, ctx->bynorm2, ctx->s);
-    if (!cs) {
-      g = launch_colnorm2(BhYh, m, m, n, ctx->colp, ctx->s);
-      launch_reduce_parts(ctx->colp, g, m, ctx->bynorm2 + m, ctx->s);
-    }
-    launch_residual_check(ctx->part, gm, ne, m, ctx->bynorm2, cs ? 1 : 2, inner_tol, ctx->d_maxrel, ctx->d_done,
-                          ctx->s);
-    ctx->inner_steps = 1;
   } else {
+    // banded direct solves with iterative refinement: FP32 factors (chosen
+    // form) or FP64 factors (plain form; the unpivoted factors of a general
+    // pencil can lose accuracy, which the refinement restores or reports)
+    const bool f32 = fp32(ctx);
     CKC(cudaMemsetAsync(ctx->d_done, 0, sizeof(int), ctx->s));
-    // the first solve takes the right-hand sides in single precision (the
-    // factors' precision; the refinement restores the rest): they are staged
-    // in the first n x m entries of the residual buffers, which the first
-    // residual overwrites
-    launch_to_cxf(BY, (cxf *)ctx->Rn, (size_t)n * m, ctx->s);
-    if (!cs) launch_to_cxf(BhYh, (cxf *)ctx->Rhn, (size_t)n * m, ctx->s);
-    int k0 = ev_begin(ctx, ctx->ev_solve);
-    CKC(band_solve_sides<float, float>(n, ctx->klp, ctx->kup, ne, ctx->fmap.data(), (const cxf *)ctx->band,
-                                       (const cxf *)ctx->dinv, (const cxf *)ctx->Rn,
-                                       cs ? nullptr : (const cxf *)ctx->Rhn, 0, m, ctx->Xn, cs ? nullptr : ctx->Xhn,
-                                       xns, 0, (cxf *)ctx->ysc, nullptr, ctx->s, tma_ptr(ctx), ctx->d_err));
-    ev_end(ctx, ctx->ev_solve, k0);
+    auto solve = [&](const void *rR, const void *rL, size_t rns, int mode) {
+      const int k = ev_begin(ctx, ctx->ev_solve);
+      if (f32)
+        CKC(band_solve_sides<float, float>(n, ctx->klp, ctx->kup, ne, ctx->fmap.data(), (const cxf *)ctx->band,
+                                           (const cxf *)ctx->dinv, (const cxf *)rR, (const cxf *)rL, rns, m,
+                                           ctx->Xn, cs ? nullptr : ctx->Xhn, xns, mode, (cxf *)ctx->ysc, nullptr,
+                                           ctx->s, tma_ptr(ctx), ctx->d_err));
+      else
+        CKC(band_solve_sides<double, double>(n, ctx->klp, ctx->kup, ne, ctx->fmap.data(), (const cxd *)ctx->band,
+                                             nullptr, (const cxd *)rR, (const cxd *)rL, rns, m, ctx->Xn,
+                                             cs ? nullptr : ctx->Xhn, xns, mode, (cxd *)ctx->ysc, nullptr, ctx->s));
+      ev_end(ctx, ctx->ev_solve, k);
+    };
+    if (f32) {
+      // the first solve takes the right-hand sides in single precision (the
+      // factors' precision; the refinement restores the rest): they are
+      // staged in the first n x m entries of the residual buffers, which the
+      // first residual overwrites
+      launch_to_cxf(BY, (cxf *)ctx->Rn, (size_t)n * m, ctx->s);
+      if (!cs) launch_to_cxf(BhYh, (cxf *)ctx->Rhn, (size_t)n * m, ctx->s);
+      solve(ctx->Rn, cs ? nullptr : ctx->Rhn, 0, 0);
+    } else {
+      solve(BY, cs ? nullptr : BhYh, 0, 0);
+    }
     int g = launch_colnorm2(BY, m, m, n, ctx->colp, ctx->s);
     launch_reduce_parts(ctx->colp, g, m, ctx->bynorm2, ctx->s);
     if (!cs) {
@@ -320,15 +317,22 @@ void do_filter(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, cxd *Q, cxd *Qh, 
     }
     const int steps = ctx->o.inner_max < 1 ? 1 : ctx->o.inner_max;
     for (int it = 0; it < steps; ++it) {
-      int kr = ev_begin(ctx, ctx->ev_resid);
       // residuals only: the node sum Q is formed once, from the final X
-      const int gm = launch_multishift_residual<float>(ctx->A, Bp, ne, ctx->dz, ctx->dw, ctx->Xn, BY, (cxf *)ctx->Rn,
-                                                       nullptr, ctx->part, m, nullptr, ctx->s);
+      int kr = ev_begin(ctx, ctx->ev_resid);
+      const int gm = f32 ? launch_multishift_residual<float>(ctx->A, Bp, ne, ctx->dz, ctx->dw, ctx->Xn, BY,
+                                                             (cxf *)ctx->Rn, nullptr, ctx->part, m, nullptr, ctx->s)
+                         : launch_multishift_residual<double>(ctx->A, Bp, ne, ctx->dz, ctx->dw, ctx->Xn, BY,
+                                                              (cxd *)ctx->Rn, nullptr, ctx->part, m, nullptr, ctx->s);
       ev_end(ctx, ctx->ev_resid, kr);
       if (!cs) {
         kr = ev_begin(ctx, ctx->ev_resid);
-        launch_multishift_residual<float>(ctx->AH, BHp, ne, ctx->dzc, ctx->dwc, ctx->Xhn, BhYh, (cxf *)ctx->Rhn,
-                                          nullptr, ctx->part + (size_t)gm * ne * m, m, nullptr, ctx->s);
+        double *pl = ctx->part + (size_t)gm * ne * m;
+        if (f32)
+          launch_multishift_residual<float>(ctx->AH, BHp, ne, ctx->dzc, ctx->dwc, ctx->Xhn, BhYh, (cxf *)ctx->Rhn,
+                                            nullptr, pl, m, nullptr, ctx->s);
+        else
+          launch_multishift_residual<double>(ctx->AH, BHp, ne, ctx->dzc, ctx->dwc, ctx->Xhn, BhYh, (cxd *)ctx->Rhn,
+                                             nullptr, pl, m, nullptr, ctx->s);
         ev_end(ctx, ctx->ev_resid, kr);
       }
       launch_residual_check(ctx->part, gm, ne, m, ctx->bynorm2, cs ? 1 : 2, inner_tol, ctx->d_maxrel, ctx->d_done,
@@ -340,15 +344,7 @@ void do_filter(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, cxd *Q, cxd *Qh, 
       std::memcpy(&done, ctx->h_small + 2, sizeof(int));
       ctx->inner_steps = it + 1;
       if (done) break;
-      if (it + 1 < steps) {
-        int ks = ev_begin(ctx, ctx->ev_solve);
-        CKC(band_solve_sides<float, float>(n, ctx->klp, ctx->kup, ne, ctx->fmap.data(), (const cxf *)ctx->band,
-                                           (const cxf *)ctx->dinv, (const cxf *)ctx->Rn,
-                                           cs ? nullptr : (const cxf *)ctx->Rhn, xns, m, ctx->Xn,
-                                           cs ? nullptr : ctx->Xhn, xns, 1, (cxf *)ctx->ysc, nullptr, ctx->s,
-                                           tma_ptr(ctx), ctx->d_err));
-        ev_end(ctx, ctx->ev_solve, ks);
-      }
+      if (it + 1 < steps) solve(ctx->Rn, cs ? nullptr : ctx->Rhn, xns, 1);
     }
     launch_node_sum(ne, ctx->dw, ctx->Xn, xns, n, m, Q, ctx->s);
     if (!cs) launch_node_sum(ne, ctx->dwc, ctx->Xhn, xns, n, m, Qh, ctx->s);
@@ -385,6 +381,23 @@ bool inner_missed(const feast_nh_ctx *ctx) {
   if (krylov(ctx)) return !ctx->krylov_ok;
   const double r = ctx->h_small[0];
   return !(r <= ctx->last_inner_tol);
+}
+
+// Step 5.d: the converged pairs first, normalised (||x|| = 1, largest entry
+// real > 0, x^^H B x = 1), from the Ritz blocks Y, Yh (n x mt, ld mt).
+void finalize_output(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, int mt, int mout, cxd *X, cxd *Xh, int ldo,
+                     double *lambda, double *res) {
+  cudaStream_t s = ctx->s;
+  const int n = ctx->n;
+  const cxd *BYf = Y;
+  if (ctx->hasB) {
+    launch_spmm(ctx->B, nullptr, nullptr, Y, ctx->T1, mt, nullptr, nullptr, s);
+    BYf = ctx->T1;
+  }
+  const int gp = launch_colstats(Y, Yh, BYf, mt, n, ctx->pn, ctx->pmax, ctx->pidx, ctx->pval, ctx->pdot, s);
+  launch_finalize(mt, gp, ctx->pn, ctx->pmax, ctx->pidx, ctx->pval, ctx->pdot, ctx->sx, ctx->sxh, Y, Yh, n,
+                  ctx->ord, mout, X, Xh, ldo, ctx->lam, ctx->res, lambda, res, s);
+  check_launch(ctx, "output");
 }
 
 RRParams rr_params(const feast_nh_ctx *ctx) {
@@ -505,6 +518,7 @@ void feast_nh_default_opts(feast_nh_opts *o) {
   o->inner_kind = FEAST_NH_INNER_BANDED;
   o->precision = FEAST_NH_PREC_FP64;
   o->problem = FEAST_NH_PROBLEM_GENERAL;
+  o->krylov_max = 1000;
 }
 
 const char *feast_nh_strerror(feast_nh_status s) {
@@ -551,16 +565,20 @@ void feast_nh_destroy(feast_nh_ctx *ctx) {
       cudaEventDestroy(p->a[k]);
       cudaEventDestroy(p->b[k]);
     }
+  if (ctx->own_stream && ctx->s) cudaStreamDestroy(ctx->s);
   delete ctx;
 }
 
-feast_nh_status feast_nh_init(feast_nh_ctx **out, const feast_nh_csr *A, const feast_nh_csr *B,
-                              const feast_nh_contour *contour, int32_t m0, const feast_nh_opts *opts,
-                              void *stream) {
-  if (!out) return FEAST_NH_EINVAL;
-  *out = nullptr;
-  feast_nh_ctx *ctx = new feast_nh_ctx();
-  try {
+}  // extern "C"
+
+namespace {
+
+// Context set-up shared by feast_nh_init and the problems of a batch
+// (rr_only: no inner-solver workspace; the batch solves the shifted systems).
+// Throws Fail.
+void init_ctx(feast_nh_ctx *ctx, const feast_nh_csr *A, const feast_nh_csr *B, const feast_nh_contour *contour,
+              int32_t m0, const feast_nh_opts *opts, void *stream, bool rr_only) {
+  {
     REQ(A && A->rowptr && A->colind && A->val && A->n > 0 && A->nnz > 0, "A must be a non-empty device CSR");
     REQ(A->dtype == FEAST_NH_R64 || A->dtype == FEAST_NH_C64, "A.dtype must be R64 or C64");
     REQ(!B || (B->rowptr && B->colind && B->val && B->n == A->n && B->nnz > 0), "B must match A's order");
@@ -583,6 +601,7 @@ feast_nh_status feast_nh_init(feast_nh_ctx **out, const feast_nh_csr *A, const f
     REQ(ctx->o.max_iter >= 1 && ctx->o.eps > 0 && ctx->o.eta >= 0 && ctx->o.mu > 0, "bad tolerances");
     REQ((size_t)contour->ne * m0 <= 2048, "ne * m0 must not exceed 2048");
     ctx->s = reinterpret_cast<cudaStream_t>(stream);
+    ctx->rr_only = rr_only;
     ctx->n = A->n;
     ctx->m0 = m0;
     ctx->ne = contour->ne;
@@ -663,7 +682,7 @@ feast_nh_status feast_nh_init(feast_nh_ctx **out, const feast_nh_csr *A, const f
       CKC(cudaMemcpyAsync(ctx->dzf, zf.data(), ctx->nf * sizeof(cxd), cudaMemcpyHostToDevice, ctx->s));
     }
     const bool f32 = fp32(ctx);
-    const bool fits = krylov(ctx) || (f32 ? (band_fits<float>(ctx->klp, ctx->kup) &&
+    const bool fits = rr_only || krylov(ctx) || (f32 ? (band_fits<float>(ctx->klp, ctx->kup) &&
                              (band_tma_fits(ctx->klp, ctx->kup) || band_solve_fits<float>(ctx->klp, ctx->kup)))
                           : (band_fits<double>(ctx->klp, ctx->kup) && band_solve_fits<double>(ctx->klp, ctx->kup)));
     if (!fits) {
@@ -672,26 +691,29 @@ feast_nh_status feast_nh_init(feast_nh_ctx **out, const feast_nh_csr *A, const f
       REQ(false, msg);
     }
     const size_t es = f32 ? sizeof(cxf) : sizeof(cxd);
-    const size_t band_elems = krylov(ctx) ? 0 : (size_t)ctx->nf * n * (ctx->klp + ctx->kup + 1);
+    const bool inner = !rr_only;
+    const size_t band_elems = (krylov(ctx) || !inner) ? 0 : (size_t)ctx->nf * n * (ctx->klp + ctx->kup + 1);
     ctx->band = dalloc<void>(ctx, band_elems * es);
-    if (krylov(ctx)) ctx->kwork = dalloc<void>(ctx, krylov_work_bytes(n, m0, ne));
-    if (f32 && !krylov(ctx) && band_tma_fits(ctx->klp, ctx->kup)) {
+    if (krylov(ctx) && inner) ctx->kwork = dalloc<void>(ctx, krylov_work_bytes(n, m0, ne));
+    if (inner && f32 && !krylov(ctx) && band_tma_fits(ctx->klp, ctx->kup)) {
       ctx->bandT = dalloc<void>(ctx, band_elems * es);
       ctx->tma.assign(band_tma_bytes(), 0);
       if (!band_tma_make(ctx->tma.data(), n, ctx->klp, ctx->kup, ctx->nf, (const cxf *)ctx->band,
                          (const cxf *)ctx->bandT))
         ctx->tma.clear();
     }
-    const size_t yse = krylov(ctx) ? 0
+    const size_t yse = (krylov(ctx) || !inner) ? 0
                        : f32   ? band_solve_scratch_elems<float>(n, m0, ne)
                                : band_solve_scratch_elems<double>(n, m0, ne);
     ctx->ysc = dalloc<void>(ctx, yse * es);
-    if (f32 && !krylov(ctx)) ctx->dinv = dalloc<void>(ctx, band_diag_inv_elems(n, ctx->nf) * sizeof(cxf));
+    if (inner && f32 && !krylov(ctx)) ctx->dinv = dalloc<void>(ctx, band_diag_inv_elems(n, ctx->nf) * sizeof(cxf));
     const size_t blk = (size_t)n * m0 * sizeof(cxd);
-    ctx->Yw = dalloc<cxd>(ctx, blk);
-    ctx->Yhw = dalloc<cxd>(ctx, blk);
-    ctx->Qw = dalloc<cxd>(ctx, blk);
-    ctx->Qhw = dalloc<cxd>(ctx, blk);
+    if (inner) {
+      ctx->Yw = dalloc<cxd>(ctx, blk);
+      ctx->Yhw = dalloc<cxd>(ctx, blk);
+      ctx->Qw = dalloc<cxd>(ctx, blk);
+      ctx->Qhw = dalloc<cxd>(ctx, blk);
+    }
     ctx->Uw = dalloc<cxd>(ctx, blk);
     ctx->Uhw = dalloc<cxd>(ctx, blk);
     ctx->T1 = dalloc<cxd>(ctx, blk);
@@ -700,14 +722,17 @@ feast_nh_status feast_nh_init(feast_nh_ctx **out, const feast_nh_csr *A, const f
       ctx->BYw = dalloc<cxd>(ctx, blk);
       ctx->BhYw = dalloc<cxd>(ctx, blk);
     }
-    ctx->Xn = dalloc<cxd>(ctx, blk * ne);
-    ctx->Xhn = dalloc<cxd>(ctx, blk * ne);
-    if (f32) {
-      ctx->Rn = dalloc<void>(ctx, (size_t)n * m0 * ne * sizeof(cxf));
-      ctx->Rhn = dalloc<void>(ctx, (size_t)n * m0 * ne * sizeof(cxf));
+    if (inner) {
+      ctx->Xn = dalloc<cxd>(ctx, blk * ne);
+      ctx->Xhn = dalloc<cxd>(ctx, blk * ne);
+    }
+    if (inner && !krylov(ctx)) {
+      // refinement residuals in the factors' precision
+      ctx->Rn = dalloc<void>(ctx, (size_t)n * m0 * ne * es);
+      ctx->Rhn = dalloc<void>(ctx, (size_t)n * m0 * ne * es);
     }
     ctx->gmax = spmm_max_grid();
-    ctx->part = dalloc<double>(ctx, (size_t)2 * ctx->gmax * 2048 * sizeof(double));
+    ctx->part = dalloc<double>(ctx, inner ? (size_t)2 * ctx->gmax * 2048 * sizeof(double) : 16);
     ctx->bynorm2 = dalloc<double>(ctx, 2 * kMaxM0 * sizeof(double));
     ctx->d_done = dalloc<int>(ctx, sizeof(int));
     ctx->d_err = dalloc<int>(ctx, sizeof(int));
@@ -753,10 +778,23 @@ feast_nh_status feast_nh_init(feast_nh_ctx **out, const feast_nh_csr *A, const f
     CKC(cudaMallocHost((void **)&ctx->h_small, 4 * sizeof(double)));
     CKC(cudaStreamSynchronize(ctx->s));
     check_launch(ctx, "init");
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+feast_nh_status feast_nh_init(feast_nh_ctx **out, const feast_nh_csr *A, const feast_nh_csr *B,
+                              const feast_nh_contour *contour, int32_t m0, const feast_nh_opts *opts,
+                              void *stream) {
+  if (!out) return FEAST_NH_EINVAL;
+  *out = nullptr;
+  feast_nh_ctx *ctx = new feast_nh_ctx();
+  try {
+    init_ctx(ctx, A, B, contour, m0, opts, stream, false);
   } catch (const Fail &f) {
-    std::string msg = ctx->err;
     feast_nh_destroy(ctx);
-    (void)msg;
     return f.st;
   }
   *out = ctx;
@@ -889,17 +927,7 @@ feast_nh_status feast_nh_solve(feast_nh_ctx *ctx, const void *Y0, const void *Yh
     }
     if (it > ctx->o.max_iter) it = ctx->o.max_iter;
     const int mout = ctx->h_st->m;
-    // 5.d  converged pairs first, normalised (||x|| = 1, max entry real > 0, x^^H B x = 1)
-    const cxd *BYf = ctx->Yw;
-    if (ctx->hasB) {
-      launch_spmm(ctx->B, nullptr, nullptr, ctx->Yw, ctx->T1, mt, nullptr, nullptr, s);
-      BYf = ctx->T1;
-    }
-    const int gp = launch_colstats(ctx->Yw, ctx->Yhw, BYf, mt, n, ctx->pn, ctx->pmax, ctx->pidx, ctx->pval,
-                                   ctx->pdot, s);
-    launch_finalize(mt, gp, ctx->pn, ctx->pmax, ctx->pidx, ctx->pval, ctx->pdot, ctx->sx, ctx->sxh, ctx->Yw,
-                    ctx->Yhw, n, ctx->ord, mout, (cxd *)X, (cxd *)Xh, m0, ctx->lam, ctx->res, lambda, res, s);
-    check_launch(ctx, "output");
+    finalize_output(ctx, ctx->Yw, ctx->Yhw, mt, mout, (cxd *)X, (cxd *)Xh, m0, lambda, res);
     CKC(cudaEventRecord(ctx->ev[3], s));
     CKC(cudaStreamSynchronize(s));
     float tot = 0;
@@ -953,6 +981,24 @@ feast_nh_status feast_nh_solve(feast_nh_ctx *ctx, const void *Y0, const void *Yh
 
 uint64_t feast_nh_kernel_launches(void) { return g_launches.load(); }
 
+feast_nh_status feast_nh_multishift_spmm(feast_nh_ctx *ctx, const void *P, void *V, int32_t m, int32_t side) {
+  if (!ctx) return FEAST_NH_EINVAL;
+  try {
+    REQ(P && V && m >= 1 && m <= ctx->m0 && (side == 0 || side == 1), "multishift_spmm: bad arguments");
+    REQ(!ctx->rr_only, "multishift_spmm: context has no operator");
+    if (side == 0)
+      launch_multishift_spmm_f32(ctx->A, ctx->hasB ? &ctx->B : nullptr, ctx->ne, ctx->dz, 0, (const cxf *)P,
+                                 (cxf *)V, m, 0, ctx->s);
+    else
+      launch_multishift_spmm_f32(ctx->AH, ctx->hasB ? &ctx->BH : nullptr, ctx->ne, ctx->dz, 1, (const cxf *)P,
+                                 (cxf *)V, m, 0, ctx->s);
+    check_launch(ctx, "multishift_spmm");
+  } catch (const Fail &f) {
+    return f.st;
+  }
+  return FEAST_NH_OK;
+}
+
 feast_nh_status feast_nh_small_eig(feast_nh_ctx *ctx, const void *M, int32_t m, void *lambda, void *V) {
   if (!ctx) return FEAST_NH_EINVAL;
   try {
@@ -995,6 +1041,452 @@ feast_nh_status feast_nh_multishift_residual(feast_nh_ctx *ctx, const void *X, c
     return f.st;
   }
   return FEAST_NH_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Many independent problems (Sec. 4.1: contours are independent): the contour
+// integration of every problem runs in one persistent launch (batch.cu); the
+// Rayleigh-Ritz step of each problem runs on that problem's own stream, all
+// problems concurrently, with the single-problem kernels.
+// ---------------------------------------------------------------------------
+struct feast_nh_batch {
+  int nprob = 0, ne = 0, m0 = 0;
+  size_t ntot = 0;
+  cudaStream_t s = nullptr;
+  feast_nh_opts o{};
+  std::vector<feast_nh_ctx *> ctx;
+  std::vector<BatchProb> hp;
+  std::vector<int> mt, conv, iters, mfound;
+  BatchProb *dprob = nullptr;
+  BatchTile *dtiles = nullptr;
+  int ntiles = 0, tile_rows = 128, threads = 256, grid = 0, max_tiles = 0;
+  cxd *Y = nullptr, *Yh = nullptr, *Q = nullptr, *Qh = nullptr, *diag = nullptr, *X = nullptr;
+  BatchLaunch L{};
+  BatchStats *h_stats = nullptr;
+  int *h_err = nullptr;
+  std::vector<void *> allocs;
+  std::string err;
+  cudaEvent_t ev[4] = {};
+  std::vector<cudaEvent_t> ev_rr;
+  double t_autotune = 0;
+  int krylov_its = 0, refine_steps = 0, inner_fail = 0;
+  double inner_res = 0;
+};
+
+namespace {
+
+#define BCK(...)                                                                           \
+  do {                                                                                     \
+    cudaError_t e_ = (__VA_ARGS__);                                                        \
+    if (e_ != cudaSuccess) {                                                               \
+      b->err = std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_);                  \
+      throw Fail{e_ == cudaErrorMemoryAllocation ? FEAST_NH_ENOMEM : FEAST_NH_ECUDA};      \
+    }                                                                                      \
+  } while (0)
+#define BREQ(cond, msg)                  \
+  do {                                   \
+    if (!(cond)) {                       \
+      b->err = msg;                      \
+      throw Fail{FEAST_NH_EINVAL};       \
+    }                                    \
+  } while (0)
+
+template <typename P>
+P *balloc(feast_nh_batch *b, size_t bytes) {
+  void *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  BCK(cudaMalloc(&p, bytes));
+  b->allocs.push_back(p);
+  return reinterpret_cast<P *>(p);
+}
+
+bool batch_fp32(const feast_nh_batch *b) { return b->o.precision == FEAST_NH_PREC_FP32_IR; }
+
+// Tiles of `rows` consecutive rows of one problem, problems in order.
+void batch_tiles(feast_nh_batch *b, int rows) {
+  std::vector<BatchTile> t;
+  for (int p = 0; p < b->nprob; ++p) {
+    b->hp[p].tb = (int)t.size();
+    for (int r0 = 0; r0 < b->hp[p].n; r0 += rows) t.push_back(BatchTile{p, r0, std::min(b->hp[p].n, r0 + rows), 0});
+    b->hp[p].te = (int)t.size();
+  }
+  b->ntiles = (int)t.size();
+  BREQ(b->ntiles <= b->max_tiles, "batch: tile table overflow");
+  // pageable host sources: these copies complete before the call returns
+  BCK(cudaMemcpyAsync(b->dtiles, t.data(), t.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, b->s));
+  BCK(cudaMemcpyAsync(b->dprob, b->hp.data(), b->hp.size() * sizeof(BatchProb), cudaMemcpyHostToDevice, b->s));
+  BCK(cudaStreamSynchronize(b->s));
+  b->tile_rows = rows;
+}
+
+void batch_upload_probs(feast_nh_batch *b) {
+  BCK(cudaMemcpyAsync(b->dprob, b->hp.data(), b->hp.size() * sizeof(BatchProb), cudaMemcpyHostToDevice, b->s));
+}
+
+// One launch of the batched contour integration; returns after the launch is
+// enqueued.  tol: refinement target of the shifted solves.
+void batch_filter_run(feast_nh_batch *b, double tol, int nsteps, int kmax) {
+  b->L.ntiles = b->ntiles;
+  b->L.tol = tol;
+  b->L.nsteps = nsteps;
+  b->L.kmax = kmax;
+  const cudaError_t e = batch_fp32(b) ? batch_filter_launch<float>(b->L, b->grid, b->threads, b->s)
+                                      : batch_filter_launch<double>(b->L, b->grid, b->threads, b->s);
+  BCK(e);
+}
+
+// Project autotuner: times the persistent launch (three Krylov iterations of
+// one refinement step on a fixed input) for each candidate shape -- threads
+// per CTA, CTAs per SM (the cooperative grid), rows per tile -- and keeps
+// the fastest.
+void batch_autotune(feast_nh_batch *b) {
+  int sms = 152, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  launch_fill_pattern(b->Y, b->ntot * b->m0, b->s);
+  launch_fill_pattern(b->Yh, b->ntot * b->m0, b->s);
+  float best = 1e30f;
+  int bt = 256, bg = 0, br = 128;
+  const int threads_c[] = {128, 256, 384, 512};
+  const int rows_c[] = {32, 128, 512};
+  BCK(cudaEventRecord(b->ev[2], b->s));
+  for (int th : threads_c) {
+    const int occ = batch_fp32(b) ? batch_filter_max_ctas_per_sm<float>(th) : batch_filter_max_ctas_per_sm<double>(th);
+    if (occ < 1) continue;
+    for (int per_sm = 1; per_sm <= std::min(occ, 4); per_sm *= 2)
+      for (int rows : rows_c) {
+        batch_tiles(b, rows);
+        b->threads = th;
+        b->grid = std::min(sms * per_sm, std::max(1, b->ntiles));
+        batch_filter_run(b, 0.0, 1, 3);
+        BCK(cudaEventRecord(b->ev[0], b->s));
+        batch_filter_run(b, 0.0, 1, 3);
+        BCK(cudaEventRecord(b->ev[1], b->s));
+        BCK(cudaEventSynchronize(b->ev[1]));
+        float ms = 0;
+        BCK(cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
+        if (ms < best) {
+          best = ms;
+          bt = th;
+          bg = b->grid;
+          br = rows;
+        }
+      }
+  }
+  BCK(cudaEventRecord(b->ev[3], b->s));
+  BCK(cudaEventSynchronize(b->ev[3]));
+  float tot = 0;
+  cudaEventElapsedTime(&tot, b->ev[2], b->ev[3]);
+  b->t_autotune = tot;
+  BREQ(bg > 0, "no launch shape of the batched solver fits this device");
+  b->threads = bt;
+  b->grid = bg;
+  batch_tiles(b, br);
+  int herr = 0;
+  BCK(cudaMemcpyAsync(&herr, b->L.err, sizeof(int), cudaMemcpyDeviceToHost, b->s));
+  BCK(cudaStreamSynchronize(b->s));
+  BREQ(!(herr & DEVERR_TIMEOUT), "a grid barrier of the batched solver gave up while tuning");
+}
+
+void batch_destroy_impl(feast_nh_batch *b) {
+  if (!b) return;
+  if (b->s) cudaStreamSynchronize(b->s);
+  for (auto *c : b->ctx) feast_nh_destroy(c);
+  for (void *p : b->allocs) cudaFree(p);
+  if (b->h_stats) cudaFreeHost(b->h_stats);
+  if (b->h_err) cudaFreeHost(b->h_err);
+  for (auto &e : b->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto &e : b->ev_rr)
+    if (e) cudaEventDestroy(e);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+feast_nh_status feast_nh_batch_init(feast_nh_batch **out, int32_t nprob, const feast_nh_csr *A,
+                                    const feast_nh_contour *contours, int32_t m0, const feast_nh_opts *opts,
+                                    void *stream) {
+  if (!out) return FEAST_NH_EINVAL;
+  *out = nullptr;
+  feast_nh_batch *b = new feast_nh_batch();
+  try {
+    BREQ(nprob >= 1 && A && contours, "batch: nprob >= 1 problems with matrices and contours");
+    BREQ(m0 >= 1 && m0 <= kMaxM0, "batch: m0 must be in [1, 128]");
+    if (opts) b->o = *opts; else feast_nh_default_opts(&b->o);
+    BREQ(b->o.inner_kind == FEAST_NH_INNER_BICGSTAB, "batch: the inner solver is BiCGStab (inner_kind)");
+    BREQ(b->o.problem == FEAST_NH_PROBLEM_GENERAL, "batch: general problems only");
+    BREQ(b->o.krylov_max >= 1 && b->o.inner_max >= 1, "batch: krylov_max and inner_max must be >= 1");
+    const int ne = contours[0].ne;
+    BREQ(ne >= 1 && ne <= kBatchMaxNe, "batch: contour.ne must be in [1, 16]");
+    b->nprob = nprob;
+    b->ne = ne;
+    b->m0 = m0;
+    b->s = reinterpret_cast<cudaStream_t>(stream);
+    b->hp.assign(nprob, BatchProb{});
+    b->mt.assign(nprob, m0);
+    b->conv.assign(nprob, 0);
+    b->iters.assign(nprob, 0);
+    b->mfound.assign(nprob, 0);
+    for (auto &e : b->ev) BCK(cudaEventCreateWithFlags(&e, cudaEventDefault));
+    // per-problem contexts (Rayleigh-Ritz workspace, transposed CSR, nodes)
+    feast_nh_opts ro = b->o;
+    ro.inner_kind = FEAST_NH_INNER_BANDED;
+    ro.precision = FEAST_NH_PREC_FP64;
+    size_t off = 0;
+    for (int p = 0; p < nprob; ++p) {
+      BREQ(contours[p].ne == ne, "batch: every contour must have the same ne");
+      BREQ(A[p].n >= m0, "batch: every problem needs n >= m0");
+      cudaStream_t sp = nullptr;
+      BCK(cudaStreamCreateWithFlags(&sp, cudaStreamNonBlocking));
+      feast_nh_ctx *c = new feast_nh_ctx();
+      c->s = sp;
+      c->own_stream = true;
+      b->ctx.push_back(c);
+      try {
+        init_ctx(c, &A[p], nullptr, &contours[p], m0, &ro, sp, true);
+      } catch (const Fail &f) {
+        b->err = "batch problem " + std::to_string(p) + ": " + c->err;
+        throw;
+      }
+      c->own_stream = true;
+      BatchProb &bp = b->hp[p];
+      bp.A = c->A;
+      bp.AH = c->AH;
+      bp.off = off;
+      bp.n = A[p].n;
+      bp.m = m0;
+      bp.active = 1;
+      for (int j = 0; j < ne; ++j) {
+        bp.z[j] = c->hz[j];
+        bp.w[j] = c->hw[j];
+      }
+      off += (size_t)A[p].n;
+      cudaEvent_t e = nullptr;
+      BCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      b->ev_rr.push_back(e);
+    }
+    b->ntot = off;
+    const size_t blk = b->ntot * m0;         // right-hand-side block elements
+    const size_t nblk = blk * ne;            // node-major block elements
+    const size_t es = batch_fp32(b) ? sizeof(cxf) : sizeof(cxd);
+    b->Y = balloc<cxd>(b, blk * sizeof(cxd));
+    b->Yh = balloc<cxd>(b, blk * sizeof(cxd));
+    b->Q = balloc<cxd>(b, blk * sizeof(cxd));
+    b->Qh = balloc<cxd>(b, blk * sizeof(cxd));
+    b->X = balloc<cxd>(b, nblk * sizeof(cxd));
+    b->diag = balloc<cxd>(b, b->ntot * sizeof(cxd));
+    for (int p = 0; p < nprob; ++p) launch_csr_diag(b->hp[p].A, b->diag + b->hp[p].off, b->s);
+    for (int k = 0; k < 9; ++k) b->L.kblk[k] = balloc<void>(b, nblk * es);
+    // tiles: room for the smallest tile size the tuner tries
+    int maxt = 0;
+    for (int p = 0; p < nprob; ++p) maxt += ceil_div(b->hp[p].n, 32);
+    b->max_tiles = maxt;
+    b->dtiles = balloc<BatchTile>(b, (size_t)maxt * sizeof(BatchTile));
+    b->dprob = balloc<BatchProb>(b, (size_t)nprob * sizeof(BatchProb));
+    const size_t PS = (size_t)ne * m0;
+    b->L.part = balloc<void>(b, (size_t)maxt * 2 * PS * es);
+    b->L.partd = balloc<double>(b, (size_t)maxt * PS * sizeof(double));
+    b->L.partb = balloc<double>(b, (size_t)maxt * m0 * sizeof(double));
+    const size_t S = (size_t)nprob * PS;
+    BatchScal &sc = b->L.sc;
+    sc.rho = balloc<cxd>(b, S * sizeof(cxd));
+    sc.alpha = balloc<cxd>(b, S * sizeof(cxd));
+    sc.omega = balloc<cxd>(b, S * sizeof(cxd));
+    sc.beta = balloc<cxd>(b, S * sizeof(cxd));
+    sc.bn2 = balloc<double>(b, (size_t)nprob * m0 * sizeof(double));
+    sc.rel = balloc<double>(b, S * sizeof(double));
+    sc.stop2 = balloc<double>(b, S * sizeof(double));
+    sc.act = balloc<int>(b, S * sizeof(int));
+    sc.act0 = balloc<int>(b, S * sizeof(int));
+    b->L.bar = balloc<unsigned>(b, 4 * sizeof(unsigned));
+    b->L.ctl = balloc<int>(b, 8 * sizeof(int));
+    b->L.stats = balloc<BatchStats>(b, sizeof(BatchStats));
+    b->L.err = balloc<int>(b, sizeof(int));
+    BCK(cudaMemsetAsync(b->L.err, 0, sizeof(int), b->s));
+    BCK(cudaMallocHost((void **)&b->h_stats, sizeof(BatchStats)));
+    BCK(cudaMallocHost((void **)&b->h_err, sizeof(int)));
+    b->L.nprob = nprob;
+    b->L.ne = ne;
+    b->L.m0 = m0;
+    b->L.side0 = 0;
+    b->L.side1 = 1;
+    b->L.prob = b->dprob;
+    b->L.tiles = b->dtiles;
+    b->L.Y = b->Y;
+    b->L.Yh = b->Yh;
+    b->L.Q = b->Q;
+    b->L.Qh = b->Qh;
+    b->L.diag = b->diag;
+    b->L.X = b->X;
+    b->L.tau_min = batch_fp32(b) ? 1e-5 : 0.0;
+    // a grid barrier waits at most ~8 s (at 2 GHz) before the launch gives up
+    b->L.spin_limit = 16000000000LL;
+    batch_upload_probs(b);
+    BCK(cudaStreamSynchronize(b->s));
+    for (auto *c : b->ctx) BCK(cudaStreamSynchronize(c->s));
+    batch_autotune(b);
+  } catch (const Fail &f) {
+    feast_nh_status st = f.st;
+    std::string msg = b->err;
+    batch_destroy_impl(b);
+    (void)msg;
+    return st;
+  }
+  *out = b;
+  return FEAST_NH_OK;
+}
+
+void feast_nh_batch_destroy(feast_nh_batch *b) { batch_destroy_impl(b); }
+
+const char *feast_nh_batch_last_error(const feast_nh_batch *b) { return b ? b->err.c_str() : ""; }
+
+feast_nh_status feast_nh_batch_solve(feast_nh_batch *b, const void *Y0, const void *Yh0, double *lambda, void *X,
+                                     void *Xh, double *res, int32_t *m_found, int32_t *iterations,
+                                     feast_nh_batch_info *info) {
+  if (!b) return FEAST_NH_EINVAL;
+  feast_nh_status ret = FEAST_NH_OK;
+  try {
+    BREQ(Y0 && Yh0 && lambda && X && Xh && res && m_found, "batch_solve: bad arguments");
+    cudaStream_t s = b->s;
+    const int np = b->nprob, m0 = b->m0;
+    BCK(cudaEventRecord(b->ev[0], s));
+    BCK(cudaMemcpyAsync(b->Y, Y0, b->ntot * m0 * sizeof(cxd), cudaMemcpyDeviceToDevice, s));
+    BCK(cudaMemcpyAsync(b->Yh, Yh0, b->ntot * m0 * sizeof(cxd), cudaMemcpyDeviceToDevice, s));
+    BCK(cudaMemsetAsync(b->L.err, 0, sizeof(int), s));
+    for (int p = 0; p < np; ++p) {
+      b->hp[p].m = m0;
+      b->hp[p].active = 1;
+      b->mt[p] = m0;
+      b->conv[p] = 0;
+      b->iters[p] = 0;
+      b->mfound[p] = 0;
+      b->ctx[p]->have_prev = 0;
+    }
+    b->krylov_its = b->refine_steps = b->inner_fail = 0;
+    b->inner_res = 0;
+    double t_filter = 0, t_rr = 0;
+    int it = 0;
+    std::vector<feast_nh_status> pst(np, FEAST_NH_OK);
+    for (it = 1; it <= b->o.max_iter; ++it) {
+      batch_upload_probs(b);
+      BCK(cudaEventRecord(b->ev[1], s));
+      // the first outer iteration only supplies the start subspace of the
+      // second: its shifted solves stop at a relative residual of 1e-2
+      const double tol_it = it == 1 ? std::fmax(b->o.inner_tol, 1e-2) : b->o.inner_tol;
+      batch_filter_run(b, tol_it, b->o.inner_max, b->o.krylov_max);
+      BCK(cudaMemcpyAsync(b->h_stats, b->L.stats, sizeof(BatchStats), cudaMemcpyDeviceToHost, s));
+      BCK(cudaMemcpyAsync(b->h_err, b->L.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+      BCK(cudaEventRecord(b->ev[2], s));
+      // Rayleigh-Ritz of every active problem on its own stream, concurrently
+      std::vector<std::thread> th;
+      for (int p = 0; p < np; ++p) {
+        if (!b->hp[p].active) continue;
+        th.emplace_back([b, p, &pst]() {
+          feast_nh_ctx *c = b->ctx[p];
+          try {
+            if (cudaStreamWaitEvent(c->s, b->ev[2], 0) != cudaSuccess) throw Fail{FEAST_NH_ECUDA};
+            const size_t o = b->hp[p].off * b->m0;
+            const int mt = do_rr(c, b->Q + o, b->Qh + o, b->hp[p].m, b->Y + o, b->Yh + o);
+            read_status(c);
+            b->mt[p] = mt;
+            b->conv[p] = c->h_st->conv;
+            b->mfound[p] = c->h_st->m;
+            if (cudaEventRecord(b->ev_rr[p], c->s) != cudaSuccess) throw Fail{FEAST_NH_ECUDA};
+          } catch (const Fail &f) {
+            pst[p] = f.st;
+          }
+        });
+      }
+      for (auto &t : th) t.join();
+      for (int p = 0; p < np; ++p) {
+        if (pst[p] != FEAST_NH_OK) {
+          b->err = "batch problem " + std::to_string(p) + ": " + b->ctx[p]->err;
+          throw Fail{pst[p]};
+        }
+        if (b->hp[p].active) BCK(cudaStreamWaitEvent(s, b->ev_rr[p], 0));
+      }
+      BCK(cudaEventRecord(b->ev[3], s));
+      BCK(cudaEventSynchronize(b->ev[3]));
+      float a = 0, c = 0;
+      cudaEventElapsedTime(&a, b->ev[1], b->ev[2]);
+      cudaEventElapsedTime(&c, b->ev[2], b->ev[3]);
+      t_filter += a;
+      t_rr += c;
+      if (*b->h_err & DEVERR_TIMEOUT) {
+        b->err = "a grid barrier of the batched contour integration gave up";
+        throw Fail{FEAST_NH_ETIMEOUT};
+      }
+      const BatchStats &st = *b->h_stats;
+      b->krylov_its += st.krylov_its[0] + st.krylov_its[1];
+      b->refine_steps += st.steps[0] + st.steps[1];
+      const double mr = std::fmax(__builtin_bit_cast(double, st.maxrel_bits[0]),
+                                  __builtin_bit_cast(double, st.maxrel_bits[1]));
+      b->inner_res = mr;
+      if (st.unconverged[0] + st.unconverged[1] > 0) ++b->inner_fail;
+      int nact = 0;
+      for (int p = 0; p < np; ++p) {
+        if (!b->hp[p].active) continue;
+        b->iters[p] = it;
+        if (b->conv[p]) {
+          b->hp[p].active = 0;
+        } else {
+          b->hp[p].m = b->mt[p];
+          ++nact;
+        }
+      }
+      if (nact == 0) break;
+    }
+    if (it > b->o.max_iter) it = b->o.max_iter;
+    // 5.d per problem: converged pairs first, normalised, into X, Xh (ld m0)
+    int nconv = 0;
+    double maxres = 0;
+    for (int p = 0; p < np; ++p) {
+      feast_nh_ctx *c = b->ctx[p];
+      const size_t o = b->hp[p].off * m0;
+      BCK(cudaStreamWaitEvent(c->s, b->ev[3], 0));
+      finalize_output(c, b->Y + o, b->Yh + o, b->mt[p], b->mfound[p], (cxd *)X + o, (cxd *)Xh + o, m0,
+                      lambda + (size_t)2 * p * m0, res + (size_t)p * m0);
+      BCK(cudaEventRecord(b->ev_rr[p], c->s));
+      BCK(cudaStreamWaitEvent(s, b->ev_rr[p], 0));
+      m_found[p] = b->mfound[p];
+      if (iterations) iterations[p] = b->iters[p];
+      nconv += b->conv[p] ? 1 : 0;
+      maxres = std::fmax(maxres, c->h_st->max_res);
+    }
+    BCK(cudaEventRecord(b->ev[3], s));
+    BCK(cudaEventSynchronize(b->ev[3]));
+    float tot = 0;
+    cudaEventElapsedTime(&tot, b->ev[0], b->ev[3]);
+    if (info) {
+      std::memset(info, 0, sizeof(*info));
+      info->iterations = it;
+      info->converged_problems = nconv;
+      info->inner_fail = b->inner_fail;
+      info->krylov_iterations = b->krylov_its;
+      info->refine_steps = b->refine_steps;
+      info->threads = b->threads;
+      info->tile_rows = b->tile_rows;
+      info->grid = b->grid;
+      info->max_res = maxres;
+      info->inner_res = b->inner_res;
+      info->t_filter_ms = t_filter;
+      info->t_rr_ms = t_rr;
+      info->t_total_ms = tot;
+      info->t_autotune_ms = b->t_autotune;
+    }
+    if (nconv < np) {
+      b->err = "some problems did not converge within max_iter outer iterations";
+      ret = b->inner_fail ? FEAST_NH_EINNER : FEAST_NH_ENOCONV;
+    }
+  } catch (const Fail &f) {
+    return f.st;
+  }
+  return ret;
 }
 
 }  // extern "C"

@@ -64,6 +64,11 @@ int launch_multishift_residual_capped(const CsrView &A, const CsrView *B, int ne
 // partials (each nparts x ne*m) and of bynorm2 (each m) are checked together.
 void launch_residual_check(const double *partial, int nparts, int ne, int m, const double *bynorm2, int nsides,
                            double tol, double *d_maxrel, int *d_done, cudaStream_t s);
+// FP32 multi-shift operator V_j = (z_j B - A) P_j (conj_z: conj(z_j), for the
+// conjugate-transpose CSR pair) over node-major complex-float blocks; returns
+// the grid used.  grid_per_sm <= 0: 8 CTAs of 256 threads per SM.
+int launch_multishift_spmm_f32(const CsrView &A, const CsrView *B, int ne, const cxd *d_z, int conj_z, const cxf *P,
+                               cxf *V, int m, int grid_per_sm, cudaStream_t s);
 // Out = M1 X - shift_c (M2 X)  (M2 == NULL: identity), row-major n x m blocks.
 // If p1/p2 != NULL, per-CTA partial column 1-norms of Out and of (M2 X).
 int launch_spmm(const CsrView &M1, const CsrView *M2, const cxd *shift, const cxd *X, cxd *Out, int m,
@@ -80,6 +85,65 @@ cudaError_t csr_transpose(const CsrView &A, int32_t *rowptr_t, int32_t *colind_t
 size_t krylov_work_bytes(int n, int m0, int ne);
 int krylov_bicgstab(const CsrView &A, const CsrView *B, int ne, const cxd *d_z, const cxd *d_w, const cxd *BY, int m,
                     int m0, double tol, int max_it, void *work, cxd *Xout, double *maxrel, cudaStream_t s);
+
+// ---------------- batch.cu : many problems in one persistent launch --------
+constexpr int kBatchMaxNe = 16;
+// One problem of a batch (device array).  A and AH: its CSR and conjugate
+// transpose with local column indices; rows [off, off + n) of the
+// concatenated row space; m columns per node; tiles [tb, te).
+struct BatchProb {
+  CsrView A, AH;
+  size_t off;
+  int n, m, active, tb, te, pad;
+  cxd z[kBatchMaxNe], w[kBatchMaxNe];
+};
+struct BatchTile {
+  int p, r0, r1, pad;
+};
+// Per-system state (nprob * ne * m0 entries each).
+struct BatchScal {
+  cxd *rho, *alpha, *omega, *beta;
+  double *bn2;    // ||Y_c||^2 per (problem, column): nprob * m0
+  double *rel;    // relative residual of the last refinement check
+  double *stop2;  // Krylov stopping threshold on |r|^2
+  int *act;       // iterating in the current Krylov solve
+  int *act0;      // not yet refined to tolerance
+};
+struct BatchStats {
+  unsigned long long maxrel_bits[2];
+  int unconverged[2];
+  int krylov_its[2];
+  int steps[2];
+};
+struct BatchLaunch {
+  int nprob, ne, m0, ntiles, side0, side1;
+  const BatchProb *prob;
+  const BatchTile *tiles;
+  const cxd *Y, *Yh;
+  cxd *Q, *Qh;
+  const cxd *diag;
+  cxd *X;
+  void *kblk[9];   // r, rh, p, v, y, s, z, t, d in the Krylov precision
+  void *part;
+  double *partd, *partb;
+  BatchScal sc;
+  unsigned *bar;
+  int *ctl;
+  BatchStats *stats;
+  int *err;
+  double tol, tau_min;
+  int nsteps, kmax;
+  long long spin_limit;
+};
+// Cooperative launch of the batched contour integration in precision T
+// (float: FP32 Krylov sweeps + FP64 refinement; double: plain FP64).
+template <typename T>
+cudaError_t batch_filter_launch(const BatchLaunch &L, int grid, int threads, cudaStream_t s);
+template <typename T> int batch_filter_max_ctas_per_sm(int threads);
+// diag[i] = A_ii (sum of the stored diagonal entries of row i).
+void launch_csr_diag(const CsrView &A, cxd *diag, cudaStream_t s);
+// Deterministic fill of a block with values in [-1, 1] (autotuning input).
+void launch_fill_pattern(cxd *X, size_t count, cudaStream_t s);
 
 // ---------------- dense.cu : tall-skinny and small dense kernels -----------
 // G = X^H Y (mx x my), X: n x mx (ld ldx), Y: n x my (ld ldy); partial buffer

@@ -409,3 +409,131 @@ cudaError_t csr_transpose(const CsrView &A, int32_t *rowptr_t, int32_t *colind_t
   note_launch();
   return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// FP32 multi-shift operator of the Krylov sweeps: V_j = (z_j B - A) P_j for
+// every node j and column c in one pass over A and B (left side: the
+// conjugate-transpose CSR with conj(z_j)).  P, V: node-major ne blocks of
+// n x m complex float, row-major.  One warp per (node, row) task, tasks
+// node-major so that the warps in flight sweep neighbouring rows of one node
+// (stencil neighbours are read from L2); a lane holds VW consecutive columns
+// (VW = 2: one 16-byte load per gathered row), the CSR row is read by all
+// lanes at the same address (broadcast).
+// ---------------------------------------------------------------------------
+template <int VW> struct VecF;
+template <> struct VecF<1> { using T = float2; };
+template <> struct VecF<2> { using T = float4; };
+
+template <bool CPLX>
+__device__ __forceinline__ cxf csr_valf(const CsrView &M, int64_t k) {
+  if (CPLX) {
+    const cxd v = reinterpret_cast<const cxd *>(M.val)[k];
+    return mk((float)v.re, M.conj_vals ? -(float)v.im : (float)v.im);
+  }
+  return mk((float)M.val[k], 0.f);
+}
+
+template <int VW>
+__device__ __forceinline__ void vfms(typename VecF<VW>::T &acc, cxf a, const typename VecF<VW>::T &x) {
+  // acc -= a * x (VW complex lanes)
+  acc.x = fmaf(-a.re, x.x, acc.x);
+  acc.x = fmaf(a.im, x.y, acc.x);
+  acc.y = fmaf(-a.re, x.y, acc.y);
+  acc.y = fmaf(-a.im, x.x, acc.y);
+  if constexpr (VW == 2) {
+    acc.z = fmaf(-a.re, x.z, acc.z);
+    acc.z = fmaf(a.im, x.w, acc.z);
+    acc.w = fmaf(-a.re, x.w, acc.w);
+    acc.w = fmaf(-a.im, x.z, acc.w);
+  }
+}
+template <int VW>
+__device__ __forceinline__ void vfma(typename VecF<VW>::T &acc, cxf a, const typename VecF<VW>::T &x) {
+  acc.x = fmaf(a.re, x.x, acc.x);
+  acc.x = fmaf(-a.im, x.y, acc.x);
+  acc.y = fmaf(a.re, x.y, acc.y);
+  acc.y = fmaf(a.im, x.x, acc.y);
+  if constexpr (VW == 2) {
+    acc.z = fmaf(a.re, x.z, acc.z);
+    acc.z = fmaf(-a.im, x.w, acc.z);
+    acc.w = fmaf(a.re, x.w, acc.w);
+    acc.w = fmaf(a.im, x.z, acc.w);
+  }
+}
+
+template <bool ACPLX, bool BCPLX, bool HASB, int VW>
+__global__ void __launch_bounds__(256) k_multishift_spmm_f32(CsrView A, CsrView B, int ne, const cxd *__restrict__ z,
+                                                             int conj_z, const cxf *__restrict__ P,
+                                                             cxf *__restrict__ V, int n, int m) {
+  using V4 = typename VecF<VW>::T;
+  __shared__ cxf zs[kMaxNe];
+  if (threadIdx.x < ne) {
+    const cxd zz = z[threadIdx.x];
+    zs[threadIdx.x] = mk((float)zz.re, conj_z ? -(float)zz.im : (float)zz.im);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long ntask = (long long)ne * n;
+  const size_t xns = (size_t)n * m;
+  for (long long t = warp; t < ntask; t += nwarps) {
+    const int j = (int)(t / n), i = (int)(t - (long long)j * n);
+    const cxf zj = zs[j];
+    const cxf *Pj = P + (size_t)j * xns;
+    const int64_t ka = A.rowptr[i], kae = A.rowptr[i + 1];
+    for (int c = lane * VW; c < m; c += 32 * VW) {
+      V4 acc;
+      if (HASB) {
+        V4 bx;
+        bx.x = bx.y = 0.f;
+        if constexpr (VW == 2) bx.z = bx.w = 0.f;
+        for (int64_t k = B.rowptr[i]; k < B.rowptr[i + 1]; ++k)
+          vfma<VW>(bx, csr_valf<BCPLX>(B, k), *reinterpret_cast<const V4 *>(Pj + (size_t)B.colind[k] * m + c));
+        acc.x = acc.y = 0.f;
+        if constexpr (VW == 2) acc.z = acc.w = 0.f;
+        vfma<VW>(acc, zj, bx);
+      } else {
+        acc.x = acc.y = 0.f;
+        if constexpr (VW == 2) acc.z = acc.w = 0.f;
+        vfma<VW>(acc, zj, *reinterpret_cast<const V4 *>(Pj + (size_t)i * m + c));
+      }
+#pragma unroll 4
+      for (int64_t k = ka; k < kae; ++k)
+        vfms<VW>(acc, csr_valf<ACPLX>(A, k), *reinterpret_cast<const V4 *>(Pj + (size_t)A.colind[k] * m + c));
+      *reinterpret_cast<V4 *>(V + (size_t)j * xns + (size_t)i * m + c) = acc;
+    }
+  }
+}
+
+int launch_multishift_spmm_f32(const CsrView &A, const CsrView *B, int ne, const cxd *d_z, int conj_z, const cxf *P,
+                               cxf *V, int m, int grid_per_sm, cudaStream_t s) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long ntask = (long long)ne * A.n;
+  long long g = (long long)sms * (grid_per_sm > 0 ? grid_per_sm : 8);
+  const long long need = (ntask + 7) / 8;  // 8 warps per CTA
+  if (g > need) g = need;
+  if (g < 1) g = 1;
+  CsrView Bv = B ? *B : A;
+  const bool bc = B ? B->cplx : false;
+  const bool vec2 = (m % 2) == 0;
+#define SPF(AC, BC, HB, VW) \
+  k_multishift_spmm_f32<AC, BC, HB, VW><<<(unsigned)g, 256, 0, s>>>(A, Bv, ne, d_z, conj_z, P, V, A.n, m)
+#define SPF_VW(AC, BC, HB) \
+  do {                     \
+    if (vec2) SPF(AC, BC, HB, 2); else SPF(AC, BC, HB, 1); \
+  } while (0)
+  if (!B) {
+    if (A.cplx) SPF_VW(true, false, false); else SPF_VW(false, false, false);
+  } else if (bc) {
+    if (A.cplx) SPF_VW(true, true, true); else SPF_VW(false, true, true);
+  } else {
+    if (A.cplx) SPF_VW(true, false, true); else SPF_VW(false, false, true);
+  }
+#undef SPF_VW
+#undef SPF
+  note_launch();
+  return (int)g;
+}

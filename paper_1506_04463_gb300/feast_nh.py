@@ -37,7 +37,8 @@ class ContourS(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("eps", C.c_double), ("eta", C.c_double), ("mu", C.c_double), ("inner_tol", C.c_double),
                 ("max_iter", C.c_int32), ("inner_max", C.c_int32), ("inner_kind", C.c_int32),
-                ("precision", C.c_int32), ("problem", C.c_int32), ("timing", C.c_int32)]
+                ("precision", C.c_int32), ("problem", C.c_int32), ("timing", C.c_int32),
+                ("krylov_max", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -53,10 +54,22 @@ class Info(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class BatchInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("converged_problems", C.c_int32), ("inner_fail", C.c_int32),
+                ("krylov_iterations", C.c_int32), ("refine_steps", C.c_int32), ("threads", C.c_int32),
+                ("tile_rows", C.c_int32), ("grid", C.c_int32), ("max_res", C.c_double), ("inner_res", C.c_double),
+                ("t_filter_ms", C.c_double), ("t_rr_ms", C.c_double), ("t_total_ms", C.c_double),
+                ("t_autotune_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 EXPORTS = ["feast_nh_default_opts", "feast_nh_init", "feast_nh_filter", "feast_nh_rr", "feast_nh_solve",
            "feast_nh_destroy", "feast_nh_strerror", "feast_nh_last_error", "feast_nh_nodes",
            "feast_nh_multishift_residual", "feast_nh_kernel_launches", "feast_nh_multishift_residual_noalloc",
-           "feast_nh_small_eig", "feast_nh_inject_device_error"]
+           "feast_nh_small_eig", "feast_nh_inject_device_error", "feast_nh_batch_init", "feast_nh_batch_solve",
+           "feast_nh_batch_destroy", "feast_nh_batch_last_error", "feast_nh_multishift_spmm"]
 
 _lib = None
 
@@ -86,14 +99,26 @@ def lib():
     L.feast_nh_nodes.argtypes = [C.POINTER(ContourS), C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.feast_nh_multishift_residual.argtypes = [vp, vp, vp, vp, vp, i32, i32]
     L.feast_nh_small_eig.argtypes = [vp, vp, i32, vp, vp]
+    L.feast_nh_multishift_spmm.argtypes = [vp, vp, vp, i32, i32]
     L.feast_nh_inject_device_error.argtypes = [vp, C.c_uint32]
     L.feast_nh_multishift_residual_noalloc.argtypes = [C.POINTER(Csr), C.POINTER(Csr), C.POINTER(ContourS), vp, vp,
                                                        vp, vp, vp, i32, vp]
     L.feast_nh_multishift_residual_noalloc.restype = i32
+    L.feast_nh_batch_init.argtypes = [C.POINTER(vp), i32, C.POINTER(Csr), C.POINTER(ContourS), i32, C.POINTER(Opts),
+                                      vp]
+    L.feast_nh_batch_init.restype = i32
+    L.feast_nh_batch_solve.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.POINTER(i32), C.POINTER(i32),
+                                       C.POINTER(BatchInfo)]
+    L.feast_nh_batch_solve.restype = i32
+    L.feast_nh_batch_destroy.argtypes = [vp]
+    L.feast_nh_batch_destroy.restype = None
+    L.feast_nh_batch_last_error.argtypes = [vp]
+    L.feast_nh_batch_last_error.restype = C.c_char_p
     L.feast_nh_kernel_launches.argtypes = []
     L.feast_nh_kernel_launches.restype = C.c_uint64
     for f in ("feast_nh_init", "feast_nh_filter", "feast_nh_rr", "feast_nh_solve", "feast_nh_nodes",
-              "feast_nh_multishift_residual", "feast_nh_small_eig", "feast_nh_inject_device_error"):
+              "feast_nh_multishift_residual", "feast_nh_small_eig", "feast_nh_inject_device_error",
+              "feast_nh_multishift_spmm"):
         getattr(L, f).restype = i32
     _lib = L
     return L
@@ -294,6 +319,16 @@ class FeastNH:
         self.stream.synchronize()
         return R, Q
 
+    def multishift_spmm(self, P, side=0, out=None):
+        """Single-precision multi-shift operator: V_j = (z_j B - A) P_j (side 0)
+        or (conj z_j B^H - A^H) P_j (side 1); P: (ne, n, m) complex64."""
+        if P.dtype != torch.complex64 or not P.is_contiguous():
+            raise TypeError("P must be a contiguous complex64 tensor")
+        V = torch.empty_like(P) if out is None else out
+        st = lib().feast_nh_multishift_spmm(self.h, _ptr(P), _ptr(V), P.shape[2], int(side))
+        self._check(st, "feast_nh_multishift_spmm")
+        return V
+
     def small_eig(self, M):
         """Eigenvalues and right eigenvectors of an m x m complex matrix by the
         library's small dense eigensolver (device tensors)."""
@@ -314,6 +349,76 @@ class FeastNH:
     def close(self):
         if getattr(self, "h", None):
             lib().feast_nh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class FeastBatch:
+    """Many independent standard problems (B = I) solved together: one
+    persistent launch for the contour integration of all of them, the
+    Rayleigh-Ritz steps concurrently (feast_nh_batch_* of the C ABI).
+
+    A: list of scipy CSR matrices (or device tuples from csr_to_device);
+    contours: one per problem, all with the same ne."""
+
+    def __init__(self, A, contours, m0, device="cuda", stream=None, **opts):
+        L = lib()
+        self.device = torch.device(device)
+        self.A_dev = [a if isinstance(a, tuple) else csr_to_device(a, self.device) for a in A]
+        self.sizes = [a[4] for a in self.A_dev]
+        self.offsets = np.concatenate(([0], np.cumsum(self.sizes)[:-1])).astype(np.int64)
+        self.ntot = int(sum(self.sizes))
+        self.nprob = len(self.A_dev)
+        self.m0 = int(m0)
+        opts.setdefault("inner_kind", INNER_BICGSTAB)
+        self.opts = default_opts(**opts)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        csrs = (Csr * self.nprob)(*[_csr_struct(a) for a in self.A_dev])
+        self._keep = []
+        cons = (ContourS * self.nprob)()
+        for p, c in enumerate(contours):
+            cs, keep = contour_struct(c)
+            cons[p] = cs
+            self._keep += keep
+        h = C.c_void_p()
+        st = L.feast_nh_batch_init(C.byref(h), self.nprob, csrs, cons, self.m0, C.byref(self.opts),
+                                   C.c_void_p(self.stream.cuda_stream))
+        if st != OK:
+            raise FeastError(st, "feast_nh_batch_init")
+        self.h = h
+
+    def solve(self, Y0, Yh0):
+        """Y0, Yh0: (sum n_p, m0) complex128 device tensors.  Returns per-problem
+        lists of eigenvalues, residuals, X, Xh views and the info dict."""
+        n, m0, P = self.ntot, self.m0, self.nprob
+        lam = torch.zeros(P * m0, dtype=torch.complex128, device=self.device)
+        res = torch.zeros(P * m0, dtype=torch.float64, device=self.device)
+        X = torch.zeros((n, m0), dtype=torch.complex128, device=self.device)
+        Xh = torch.zeros((n, m0), dtype=torch.complex128, device=self.device)
+        mf = (C.c_int32 * P)()
+        its = (C.c_int32 * P)()
+        info = BatchInfo()
+        Y0c, Yh0c = Y0.contiguous(), Yh0.contiguous()
+        st = lib().feast_nh_batch_solve(self.h, _ptr(Y0c), _ptr(Yh0c), _ptr(lam), _ptr(X), _ptr(Xh), _ptr(res), mf,
+                                        its, C.byref(info))
+        if st not in (OK, ENOCONV, EINNER):
+            raise FeastError(st, "feast_nh_batch_solve: " + lib().feast_nh_batch_last_error(self.h).decode())
+        out = []
+        for p in range(P):
+            o, npb, m = int(self.offsets[p]), self.sizes[p], mf[p]
+            # problem p's block: rows [o, o + n_p) of the (sum n_p, m0) arrays
+            out.append(dict(lam=lam[p * m0: p * m0 + m], res=res[p * m0: p * m0 + m], X=X[o:o + npb, :m],
+                            Xh=Xh[o:o + npb, :m], m=m, iterations=its[p]))
+        return dict(status=st, problems=out, info=info.as_dict())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().feast_nh_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

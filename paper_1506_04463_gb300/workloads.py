@@ -242,3 +242,83 @@ def pencil_workload(n: int, seed: int, ne: int = 8, m0: int = 8, complex_: bool 
     return Workload(f"pencil_n{n}_s{seed}", A, B, con, m0,
                     start_block(n, m0, 2 * seed, complex_), start_block(n, m0, 2 * seed + 1, complex_),
                     "general", np.sort_complex(ev[np.abs(ev - c) <= r]))
+
+
+def edge_circle(A: sp.csr_matrix, k_lo: int = 16, k_hi: int = 40, nev: int = 48, seed: int = 0):
+    """Circle around eigenvalues at the right edge of the spectrum of a real
+    sparse A (input construction only: ARPACK's `nev` rightmost eigenvalues).
+    Centre on the real axis just right of the rightmost eigenvalue; radius
+    halfway across the widest relative gap among the sorted distances with
+    k_lo..k_hi eigenvalues inside, and small enough that every eigenvalue it
+    can hold is among the computed ones.  Returns (contour, eigenvalues
+    inside)."""
+    import scipy.sparse.linalg as spla
+    n = A.shape[0]
+    v0 = np.random.default_rng(seed).standard_normal(n)
+    ev = spla.eigs(A.astype(np.float64), k=nev, which="LR", return_eigenvectors=False, tol=1e-12, v0=v0,
+                   ncv=min(n, max(2 * nev + 1, 120)))
+    ev = ev[np.argsort(-ev.real)]
+    c = float(ev[0].real) + 0.02
+    d = np.sort(np.abs(ev - c))
+    lo_bound = c - float(ev[-1].real)          # a radius beyond this could hold uncomputed eigenvalues
+    best = None
+    for k in range(k_lo, min(k_hi, nev - 1) + 1):
+        r = 0.5 * (d[k - 1] + d[k])
+        gap = (d[k] - d[k - 1]) / r
+        if r < 0.95 * lo_bound and (best is None or gap > best[0]):
+            best = (gap, r)
+    if best is None:
+        raise ValueError("no radius with 16..40 computed eigenvalues inside")
+    r = best[1]
+    con = Contour(0, complex(c), r)
+    return con, np.sort_complex(ev[np.abs(ev - c) <= r])
+
+
+@dataclass
+class BatchWorkload:
+    name: str
+    A: list                      # per-problem CSR matrices (B = I)
+    contours: list               # per-problem Contour
+    m0: int
+    Y0: np.ndarray               # (sum n_p) x m0, problems stacked by rows
+    Yh0: np.ndarray
+    exact: list                  # per-problem eigenvalues inside (ARPACK, for checks)
+    offsets: np.ndarray          # first row of each problem
+
+
+def _config4_problem(args):
+    p, n, m0 = args
+    Ap = random_sparse(n, 100 + p)
+    con, inside = edge_circle(Ap, seed=p)
+    return Ap, con, inside, start_block(n, m0, 2 * p), start_block(n, m0, 2 * p + 1)
+
+
+def config4(nprob: int = 64, nmin: int = 5000, nmax: int = 200000, m0: int = 48, ne: int = 8,
+            seed: int = 0, workers: int | None = None) -> BatchWorkload:
+    """Many independent random sparse nonsymmetric problems: sizes log-uniform
+    in [nmin, nmax] (seed), rows as random_sparse (seed 100 + p), B = I, each
+    with its own circle at the right edge of its spectrum holding 16..40
+    eigenvalues, m0 columns, ne trapezoid nodes; start blocks N(0,1) with
+    seeds 2p and 2p + 1.  `workers` > 1 builds the problems in that many
+    spawned processes (same result)."""
+    rng = np.random.default_rng(seed)
+    sizes = np.round(np.exp(rng.uniform(math.log(nmin), math.log(nmax), nprob))).astype(int)
+    args = [(p, int(n), m0) for p, n in enumerate(sizes)]
+    if workers and workers > 1 and nprob > 1:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(max_workers=min(workers, nprob), mp_context=mp.get_context("spawn")) as ex_:
+            parts = list(ex_.map(_config4_problem, args))
+    else:
+        parts = [_config4_problem(a) for a in args]
+    A, cons, ex, Y, Yh = [], [], [], [], []
+    for Ap, con, inside, y, yh in parts:
+        con.ne = ne
+        A.append(Ap)
+        cons.append(con)
+        ex.append(inside)
+        Y.append(y)
+        Yh.append(yh)
+    offs = np.concatenate(([0], np.cumsum(sizes)[:-1]))
+    return BatchWorkload(f"random_sparse_batch{nprob}", A, cons, m0, np.ascontiguousarray(np.vstack(Y)),
+                         np.ascontiguousarray(np.vstack(Yh)), ex, offs)

@@ -120,6 +120,29 @@ def test_multishift_residual_single_precision_output():
     ctx.close()
 
 
+@pytest.mark.parametrize("with_b,side,m", [(False, 0, 10), (True, 0, 10), (True, 1, 10), (False, 1, 9)])
+def test_multishift_spmm_single_precision(with_b, side, m):
+    # the FP32 Krylov operator against the definition (z_j B - A) P_j in FP64
+    # (m even: two columns per 16-byte lane load; m odd: one per lane)
+    wk = banded_workload(n=331, kl=6, ku=3, m0=10, ne=6, with_b=with_b)
+    ctx = make_ctx(wk, precision=F.PREC_FP32_IR)
+    z, w = contour_nodes(wk.contour)
+    rng = np.random.default_rng(5)
+    P = (rng.standard_normal((6, 331, m)) + 1j * rng.standard_normal((6, 331, m))).astype(np.complex64)
+    V = host(ctx.multishift_spmm(torch.from_numpy(P).cuda(), side=side)).astype(np.complex128)
+    A = wk.A if side == 0 else wk.A.conj().T.tocsr()
+    B = None if wk.B is None else (wk.B if side == 0 else wk.B.conj().T.tocsr())
+    zz = z if side == 0 else np.conj(z)
+    Ro, _ = OF.shifted_residuals(A, B, zz, w, P.astype(np.complex128), np.zeros((331, m)))
+    Vo = -Ro
+    # single-precision products and sums over at most 11 terms per entry
+    absA = abs(A)
+    bound = np.stack([(np.abs(zz[j]) * (np.abs(P[j]) if B is None else abs(B) @ np.abs(P[j])) + absA @ np.abs(P[j]))
+                      for j in range(6)])
+    assert np.all(np.abs(V - Vo) <= 24 * 2 ** -24 * bound + 1e-30)
+    ctx.close()
+
+
 @pytest.mark.parametrize("prec,opts", [(F.PREC_FP32_IR, dict(inner_max=1, inner_tol=1e-14)),
                                        (F.PREC_FP64, dict(inner_tol=1e-30))])
 def test_inner_solve_failure_is_reported(prec, opts):
