@@ -461,7 +461,12 @@ __device__ __forceinline__ void vfma(typename VecF<VW>::T &acc, cxf a, const typ
   }
 }
 
-template <bool ACPLX, bool BCPLX, bool HASB, int VW>
+// One warp per row i, all nodes: the row's CSR entries (up to KMAX) are
+// loaded once into registers and reused for every node j; the gathers of one
+// node (one 16-byte load per lane and entry) are independent, so a lane has
+// up to KMAX + 1 loads in flight per node.  Rows longer than KMAX, and a
+// non-identity B, take the general loop.
+template <bool ACPLX, bool BCPLX, bool HASB, int VW, int KMAX>
 __global__ void __launch_bounds__(256) k_multishift_spmm_f32(CsrView A, CsrView B, int ne, const cxd *__restrict__ z,
                                                              int conj_z, const cxf *__restrict__ P,
                                                              cxf *__restrict__ V, int n, int m) {
@@ -473,54 +478,77 @@ __global__ void __launch_bounds__(256) k_multishift_spmm_f32(CsrView A, CsrView 
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  const long long ntask = (long long)ne * n;
+  const int warp = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nwarps = (int)(((long long)gridDim.x * blockDim.x) >> 5);
   const size_t xns = (size_t)n * m;
-  for (long long t = warp; t < ntask; t += nwarps) {
-    const int j = (int)(t / n), i = (int)(t - (long long)j * n);
-    const cxf zj = zs[j];
-    const cxf *Pj = P + (size_t)j * xns;
-    const int64_t ka = A.rowptr[i], kae = A.rowptr[i + 1];
+  for (int i = warp; i < n; i += nwarps) {
+    const int64_t ka = A.rowptr[i];
+    const int nk = (int)(A.rowptr[i + 1] - ka);
+    int col[KMAX];
+    cxf av[KMAX];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+      col[k] = k < nk ? A.colind[ka + k] : i;
+      av[k] = k < nk ? csr_valf<ACPLX>(A, ka + k) : mk(0.f, 0.f);
+    }
+    const bool fast = !HASB && nk <= KMAX;
     for (int c = lane * VW; c < m; c += 32 * VW) {
-      V4 acc;
-      if (HASB) {
-        V4 bx;
-        bx.x = bx.y = 0.f;
-        if constexpr (VW == 2) bx.z = bx.w = 0.f;
-        for (int64_t k = B.rowptr[i]; k < B.rowptr[i + 1]; ++k)
-          vfma<VW>(bx, csr_valf<BCPLX>(B, k), *reinterpret_cast<const V4 *>(Pj + (size_t)B.colind[k] * m + c));
+#pragma unroll 2
+      for (int j = 0; j < ne; ++j) {
+        const cxf *Pj = P + (size_t)j * xns;
+        V4 acc;
         acc.x = acc.y = 0.f;
         if constexpr (VW == 2) acc.z = acc.w = 0.f;
-        vfma<VW>(acc, zj, bx);
-      } else {
-        acc.x = acc.y = 0.f;
-        if constexpr (VW == 2) acc.z = acc.w = 0.f;
-        vfma<VW>(acc, zj, *reinterpret_cast<const V4 *>(Pj + (size_t)i * m + c));
+        if (fast) {
+          V4 xs[KMAX];
+#pragma unroll
+          for (int k = 0; k < KMAX; ++k) xs[k] = *reinterpret_cast<const V4 *>(Pj + (size_t)col[k] * m + c);
+          vfma<VW>(acc, zs[j], *reinterpret_cast<const V4 *>(Pj + (size_t)i * m + c));
+#pragma unroll
+          for (int k = 0; k < KMAX; ++k) vfms<VW>(acc, av[k], xs[k]);
+        } else {
+          if (HASB) {
+            V4 bx;
+            bx.x = bx.y = 0.f;
+            if constexpr (VW == 2) bx.z = bx.w = 0.f;
+            for (int64_t k = B.rowptr[i]; k < B.rowptr[i + 1]; ++k)
+              vfma<VW>(bx, csr_valf<BCPLX>(B, k), *reinterpret_cast<const V4 *>(Pj + (size_t)B.colind[k] * m + c));
+            vfma<VW>(acc, zs[j], bx);
+          } else {
+            vfma<VW>(acc, zs[j], *reinterpret_cast<const V4 *>(Pj + (size_t)i * m + c));
+          }
+          for (int k = 0; k < nk; ++k)
+            vfms<VW>(acc, csr_valf<ACPLX>(A, ka + k), *reinterpret_cast<const V4 *>(Pj + (size_t)A.colind[ka + k] * m + c));
+        }
+        *reinterpret_cast<V4 *>(V + (size_t)j * xns + (size_t)i * m + c) = acc;
       }
-#pragma unroll 4
-      for (int64_t k = ka; k < kae; ++k)
-        vfms<VW>(acc, csr_valf<ACPLX>(A, k), *reinterpret_cast<const V4 *>(Pj + (size_t)A.colind[k] * m + c));
-      *reinterpret_cast<V4 *>(V + (size_t)j * xns + (size_t)i * m + c) = acc;
     }
   }
 }
 
 int launch_multishift_spmm_f32(const CsrView &A, const CsrView *B, int ne, const cxd *d_z, int conj_z, const cxf *P,
                                cxf *V, int m, int grid_per_sm, cudaStream_t s) {
+  constexpr int KMAX = 8;
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long ntask = (long long)ne * A.n;
-  long long g = (long long)sms * (grid_per_sm > 0 ? grid_per_sm : 8);
-  const long long need = (ntask + 7) / 8;  // 8 warps per CTA
-  if (g > need) g = need;
-  if (g < 1) g = 1;
   CsrView Bv = B ? *B : A;
   const bool bc = B ? B->cplx : false;
   const bool vec2 = (m % 2) == 0;
-#define SPF(AC, BC, HB, VW) \
-  k_multishift_spmm_f32<AC, BC, HB, VW><<<(unsigned)g, 256, 0, s>>>(A, Bv, ne, d_z, conj_z, P, V, A.n, m)
+  long long g = 0;
+#define SPF(AC, BC, HB, VW)                                                                                 \
+  do {                                                                                                      \
+    auto kern = k_multishift_spmm_f32<AC, BC, HB, VW, KMAX>;                                                \
+    int occ = 0;                                                                                            \
+    if (grid_per_sm > 0) occ = grid_per_sm;                                                                 \
+    else if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0) != cudaSuccess || occ < 1) \
+      occ = 1;                                                                                              \
+    g = (long long)sms * occ;                                                                               \
+    const long long need = (A.n + 7) / 8; /* 8 warps per CTA, one row each */                              \
+    if (g > need) g = need;                                                                                 \
+    if (g < 1) g = 1;                                                                                       \
+    kern<<<(unsigned)g, 256, 0, s>>>(A, Bv, ne, d_z, conj_z, P, V, A.n, m);                                 \
+  } while (0)
 #define SPF_VW(AC, BC, HB) \
   do {                     \
     if (vec2) SPF(AC, BC, HB, 2); else SPF(AC, BC, HB, 1); \

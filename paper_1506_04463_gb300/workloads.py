@@ -220,6 +220,36 @@ def banded_random(n: int, kl: int, ku: int, seed: int, complex_: bool = True) ->
     return sp.diags(diags, offs, format="csr").astype(np.complex128)
 
 
+def banded_accretive(n: int, kl: int, ku: int, seed: int, complex_: bool = True) -> sp.csr_matrix:
+    """Banded matrix that Gaussian elimination without pivoting factors
+    stably at any non-real shift: A = S^{-1} H S with H Hermitian banded
+    (half-bandwidth min(kl, ku), N(0,1) entries scaled by 1/sqrt(band)) and
+    S = diag(exp(U(-1/2, 1/2))); the wider side of an unequal band gets
+    extra diagonals of size 1e-3.  Then z I - A = S^{-1}(z I - H) S and every
+    pivot of z I - H has |Im pivot| >= |Im z| > 0."""
+    rng = np.random.default_rng(seed)
+    k = min(kl, ku)
+    H = np.zeros((n, n), np.complex128)
+    H[np.arange(n), np.arange(n)] = rng.standard_normal(n)
+    for d in range(1, k + 1):
+        v = rng.standard_normal(n - d) / math.sqrt(k)
+        if complex_:
+            v = v + 1j * rng.standard_normal(n - d) / math.sqrt(k)
+        H[np.arange(n - d), np.arange(d, n)] = v
+        H[np.arange(d, n), np.arange(n - d)] = np.conj(v)
+    for d in range(k + 1, max(kl, ku) + 1):
+        v = 1e-3 * rng.standard_normal(n - d)
+        if ku > kl:
+            H[np.arange(n - d), np.arange(d, n)] = v
+        else:
+            H[np.arange(d, n), np.arange(n - d)] = v
+    s = np.exp(rng.uniform(-0.5, 0.5, n))
+    A = (H / s[:, None]) * s[None, :]
+    if not complex_:
+        A = A.real
+    return sp.csr_matrix(A.astype(np.complex128))
+
+
 def pencil_workload(n: int, seed: int, ne: int = 8, m0: int = 8, complex_: bool = True,
                     with_b: bool = True, n_inside: int = 3) -> Workload:
     """Tiny dense pencil with a circle around the (at least) n_inside eigenvalues

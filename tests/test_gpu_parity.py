@@ -17,17 +17,25 @@ from gpu_helpers import dev, host, invariants, make_ctx, match_rel  # noqa: E402
 PRECS = [F.PREC_FP64, F.PREC_FP32_IR]
 
 
-def banded_workload(n=300, kl=5, ku=3, seed=0, m0=8, ne=8, with_b=True):
-    A = wl.banded_random(n, kl, ku, seed)
+def banded_workload(n=300, kl=5, ku=3, seed=0, m0=8, ne=8, with_b=True, pivoting=False):
+    """Banded complex pencil in the class of the unpivoted banded solver
+    (accretive shifted matrices, real positive diagonal B); pivoting=True
+    gives a random banded pencil (complex diagonal B) that needs pivoting."""
+    A = wl.banded_random(n, kl, ku, seed) if pivoting else wl.banded_accretive(n, kl, ku, seed)
     B = None
     if with_b:
         rng = np.random.default_rng(seed + 1)
-        B = sp.diags(rng.uniform(1, 2, n) * np.exp(1j * rng.uniform(-0.2, 0.2, n))).tocsr()
+        if pivoting:
+            B = sp.diags(rng.uniform(1, 2, n) * np.exp(1j * rng.uniform(-0.2, 0.2, n))).tocsr()
+        else:
+            B = sp.diags(rng.uniform(1, 2, n) + 0j).tocsr()
     import scipy.linalg as sla
     ev = sla.eigvals(A.toarray(), None if B is None else B.toarray())
     c = np.median(ev.real) + 1j * np.median(ev.imag)
     d = np.sort(np.abs(ev - c))
-    con = wl.Contour(0, complex(c), float(0.5 * (d[3] + d[4])), ne=ne)
+    # radius across the widest relative gap with 3 .. m0 - 3 eigenvalues inside
+    k = max(range(3, max(4, m0 - 2)), key=lambda k: (d[k] - d[k - 1]) / d[k])
+    con = wl.Contour(0, complex(c), float(0.5 * (d[k - 1] + d[k])), ne=ne)
     return wl.Workload(f"banded{n}", A, B, con, m0, wl.start_block(n, m0, 0, True), wl.start_block(n, m0, 1, True),
                        "general", ev[np.abs(ev - c) <= con.r])
 
@@ -245,3 +253,20 @@ def test_bicgstab_reports_unconverged_interior_systems():
     with pytest.raises(F.FeastError) as e:
         ctx.filter(dev(wk.Y0), dev(wk.Yh0))
     assert e.value.status == F.EINNER
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("case", ["banded_B", "banded_noB"])
+def test_pivoting_needed_is_reported(prec, case):
+    # random complex banded pencils need pivoting at interior shifts; the
+    # unpivoted banded solver does not pivot, and the refinement residual
+    # reports the inaccurate solves as FEAST_NH_EINNER instead of a silent result
+    if case == "banded_B":
+        wk = banded_workload(n=300, kl=5, ku=3, with_b=True, pivoting=True)
+    else:
+        wk = banded_workload(n=161, kl=2, ku=7, with_b=False, m0=5, ne=6, pivoting=True)
+    ctx = make_ctx(wk, precision=prec)
+    with pytest.raises(F.FeastError) as e:
+        ctx.filter(dev(wk.Y0), dev(wk.Yh0))
+    assert e.value.status == F.EINNER
+    ctx.close()
