@@ -319,6 +319,38 @@ feast_nh_status feast_nh_batch_solve(feast_nh_batch *batch, const void *Y0, cons
 void feast_nh_batch_destroy(feast_nh_batch *batch);
 const char *feast_nh_batch_last_error(const feast_nh_batch *batch);
 
+/* ------------------------------------------------------------------------
+ * Network of the learned preconditioner (the inner solves of step 1 accept
+ * any solver, Sec. 3; this one is trained on the method's own exact solves):
+ * `layers` 3x3 convolutions on an N x N grid, 32 channels, zero padding at
+ * the grid boundary, ReLU between layers, none after the last:
+ *     z_l = conv3x3(a_{l-1}; W_l) + b_l,  a_l = relu(z_l),  out = z_L.
+ * BF16 weights and activations, FP32 accumulation on the tensor cores
+ * (tcgen05), FP32 master parameters and Adam updates.  Images are DEVICE
+ * float arrays, channel-last (image, y, x, channel), 32 channels.  Parameters
+ * (HOST float arrays) are, per layer, W[tap][c_in][c_out] (tap = 3 dy + dx
+ * for the neighbour offset (dy - 1, dx - 1); 9 * 32 * 32 values) followed by
+ * b[32]: layers * 9248 floats in all.  All calls run on `stream` and wait for
+ * it before returning. */
+typedef struct feast_nh_net feast_nh_net; /* opaque */
+
+/* Workspace for up to max_images images; parameters start at zero. */
+feast_nh_status feast_nh_net_create(feast_nh_net **net, int32_t layers, int32_t N, int32_t max_images,
+                                    void *stream);
+feast_nh_status feast_nh_net_set_params(feast_nh_net *net, const float *params);
+feast_nh_status feast_nh_net_get_params(feast_nh_net *net, float *params);
+/* out = network(x), both nimg x N x N x 32 (device). */
+feast_nh_status feast_nh_net_forward(feast_nh_net *net, const float *x, float *out, int32_t nimg);
+/* One training step on the mean squared error of the first `cout` output
+ * channels against `target` (nimg x N x N x cout, device):
+ * loss = sum (out - target)^2 / (nimg N^2 cout).  Writes the loss (host) and,
+ * if grad != NULL, the parameter gradient (device, layers * 9248 floats);
+ * lr > 0 applies one Adam step (beta 0.9 / 0.999, eps 1e-8), lr = 0 none. */
+feast_nh_status feast_nh_net_train_step(feast_nh_net *net, const float *x, const float *target, int32_t cout,
+                                        int32_t nimg, float lr, double *loss, float *grad);
+void feast_nh_net_destroy(feast_nh_net *net);
+const char *feast_nh_net_last_error(const feast_nh_net *net);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,7 +13,10 @@ channel-last.  The loss is the mean squared error over the first `cout`
 output channels, L = sum((out[..., :cout] - target)^2) / target.size.
 
 Every function is the plain definition (explicit loops over the nine taps;
-numpy for the channel contractions), so that it can be checked by eye."""
+numpy for the channel contractions), so that it can be checked by eye.
+The input gradient returned by backward() is d loss / d input, except that
+for the layers below the top it already carries relu' of the layer it feeds
+(the gradient of the pre-activation).  Pins: tests/test_oracle_net.py."""
 from __future__ import annotations
 
 import numpy as np
@@ -40,14 +43,27 @@ def conv3x3(a, W, b):
     return z + b
 
 
-def forward(x, Ws, bs):
-    """Returns the output and the list of (input, pre-activation) of each layer."""
-    a = x
+def bf16(x):
+    """Round to bfloat16 (8-bit significand), round-to-nearest-even, as a float.
+    The rounding points of the BF16 network: weights, the input and every
+    hidden activation, and the stored gradients."""
+    f = np.ascontiguousarray(np.asarray(x, np.float32))
+    b = f.view(np.uint32).astype(np.uint64)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward(x, Ws, bs, quant=False):
+    """Returns the output and the list of (input, pre-activation) of each layer.
+    quant: round weights, input and hidden activations to bfloat16 (biases and
+    the last layer's output stay in single precision)."""
+    q = bf16 if quant else (lambda v: v)
+    a = q(x)
     cache = []
     for l, (W, b) in enumerate(zip(Ws, bs)):
-        z = conv3x3(a, W, b)
+        z = conv3x3(a, q(W), np.float32(b).astype(np.float64) if quant else b)
         cache.append((a, z))
-        a = np.maximum(z, 0.0) if l < len(Ws) - 1 else z
+        a = q(np.maximum(z, 0.0)) if l < len(Ws) - 1 else z
     return a, cache
 
 
@@ -57,16 +73,19 @@ def loss(out, target):
     return float(np.sum(d * d) / target.size)
 
 
-def backward(out, target, cache, Ws):
-    """Gradients of loss() with respect to every W_l, b_l and the input."""
+def backward(out, target, cache, Ws, quant=False):
+    """Gradients of loss() with respect to every W_l, b_l and the input.
+    quant: the bfloat16 rounding points of the BF16 network (weights, the
+    output gradient and every propagated activation gradient)."""
+    q = bf16 if quant else (lambda v: v)
+    Ws = [q(W) for W in Ws]
     cout = target.shape[-1]
     g = np.zeros_like(out)
     g[..., :cout] = 2.0 * (out[..., :cout] - target) / target.size
+    g = q(g)
     dWs, dbs = [None] * len(Ws), [None] * len(Ws)
     for l in range(len(Ws) - 1, -1, -1):
         a, z = cache[l]
-        if l < len(Ws) - 1:
-            g = g * (z > 0)                      # relu'
         dbs[l] = g.sum(axis=(0, 1, 2))
         dW = np.zeros_like(Ws[l])
         for dy, dx in TAPS:
@@ -77,5 +96,7 @@ def backward(out, target, cache, Ws):
         ga = np.zeros_like(a)
         for dy, dx in TAPS:
             ga += shift(g @ Ws[l][dy, dx].T, 2 - dy, 2 - dx)
+        if l > 0:
+            ga = q(ga * (cache[l - 1][1] > 0))        # relu' of the layer below
         g = ga
     return dWs, dbs, g

@@ -23,7 +23,9 @@
 __global__ void k_band_extent(CsrView A, int *out) {
   int kl = 0, ku = 0, bad = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) {
-    for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; ++k) {
+    const int64_t rb = A.rowptr[i], re = A.rowptr[i + 1];
+    if (rb < 0 || re < rb || re > A.nnz || (i == 0 && rb != 0)) { bad = 1; continue; }
+    for (int64_t k = rb; k < re; ++k) {
       int c = A.colind[k];
       if (c < 0 || c >= A.n) { bad = 1; continue; }
       int d = c - i;

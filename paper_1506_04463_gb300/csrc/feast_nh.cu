@@ -82,6 +82,7 @@ struct feast_nh_ctx {
   double piv_min = 0, piv_max = 0;
   unsigned inject_bits = 0;   // host-requested device error bits (testing aid)
   bool rr_only = false;       // Rayleigh-Ritz workspace only (one problem of a batch)
+  int max_nnz[2] = {0, 0};    // longest row of A and of A^H
   bool own_stream = false;
   EvPool ev_solve, ev_resid;
 };
@@ -633,19 +634,29 @@ void init_ctx(feast_nh_ctx *ctx, const feast_nh_csr *A, const feast_nh_csr *B, c
     CKC(cudaMemcpyAsync(ctx->dzc, zc.data(), ne * sizeof(cxd), cudaMemcpyHostToDevice, ctx->s));
     CKC(cudaMemcpyAsync(ctx->dwc, wc.data(), ne * sizeof(cxd), cudaMemcpyHostToDevice, ctx->s));
     ctx->A = make_view(*A);
-    ctx->AH = transpose_view(ctx, ctx->A);
     if (B) {
       ctx->hasB = true;
       ctx->B = make_view(*B);
-      ctx->BH = transpose_view(ctx, ctx->B);
     }
-    // band of (z B - A)
+    // band of (z B - A); also validates the CSR arrays (row pointers within
+    // [0, nnz] and non-decreasing, column indices in [0, n)) before any
+    // kernel scatters through them
     ctx->d_ext = dalloc<int>(ctx, 4 * sizeof(int));
     launch_band_extent(ctx->A, ctx->hasB ? &ctx->B : nullptr, ctx->d_ext, ctx->s);
     int ext[3] = {0, 0, 0};
     CKC(cudaMemcpyAsync(ext, ctx->d_ext, 3 * sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
     CKC(cudaStreamSynchronize(ctx->s));
-    REQ(ext[2] == 0, "a column index of A or B is outside [0, n)");
+    REQ(ext[2] == 0, "malformed CSR: a row pointer or a column index of A or B is out of range");
+    ctx->AH = transpose_view(ctx, ctx->A);
+    if (B) ctx->BH = transpose_view(ctx, ctx->B);
+    {
+      int *d_mx = dalloc<int>(ctx, 2 * sizeof(int));
+      CKC(cudaMemsetAsync(d_mx, 0, 2 * sizeof(int), ctx->s));
+      launch_max_row_nnz(ctx->A, d_mx, ctx->s);
+      launch_max_row_nnz(ctx->AH, d_mx + 1, ctx->s);
+      CKC(cudaMemcpyAsync(ctx->max_nnz, d_mx, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+      CKC(cudaStreamSynchronize(ctx->s));
+    }
     ctx->kl = ext[0];
     ctx->ku = ext[1];
     // stored band: kl rounded up to even and kl+ku+1 even, so that band rows and
@@ -988,10 +999,10 @@ feast_nh_status feast_nh_multishift_spmm(feast_nh_ctx *ctx, const void *P, void 
     REQ(!ctx->rr_only, "multishift_spmm: context has no operator");
     if (side == 0)
       launch_multishift_spmm_f32(ctx->A, ctx->hasB ? &ctx->B : nullptr, ctx->ne, ctx->dz, 0, (const cxf *)P,
-                                 (cxf *)V, m, 0, ctx->s);
+                                 (cxf *)V, m, 0, ctx->max_nnz[0], ctx->s);
     else
       launch_multishift_spmm_f32(ctx->AH, ctx->hasB ? &ctx->BH : nullptr, ctx->ne, ctx->dz, 1, (const cxf *)P,
-                                 (cxf *)V, m, 0, ctx->s);
+                                 (cxf *)V, m, 0, ctx->max_nnz[1], ctx->s);
     check_launch(ctx, "multishift_spmm");
   } catch (const Fail &f) {
     return f.st;

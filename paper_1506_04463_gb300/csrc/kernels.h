@@ -67,8 +67,10 @@ void launch_residual_check(const double *partial, int nparts, int ne, int m, con
 // FP32 multi-shift operator V_j = (z_j B - A) P_j (conj_z: conj(z_j), for the
 // conjugate-transpose CSR pair) over node-major complex-float blocks; returns
 // the grid used.  grid_per_sm <= 0: 8 CTAs of 256 threads per SM.
+// max_row_nnz: longest row of A (launch_max_row_nnz), selects the register row length.
 int launch_multishift_spmm_f32(const CsrView &A, const CsrView *B, int ne, const cxd *d_z, int conj_z, const cxf *P,
-                               cxf *V, int m, int grid_per_sm, cudaStream_t s);
+                               cxf *V, int m, int grid_per_sm, int max_row_nnz, cudaStream_t s);
+void launch_max_row_nnz(const CsrView &A, int *d_out, cudaStream_t s);
 // Out = M1 X - shift_c (M2 X)  (M2 == NULL: identity), row-major n x m blocks.
 // If p1/p2 != NULL, per-CTA partial column 1-norms of Out and of (M2 X).
 int launch_spmm(const CsrView &M1, const CsrView *M2, const cxd *shift, const cxd *X, cxd *Out, int m,

@@ -1,0 +1,625 @@
+// Network of the learned preconditioner: a stack of 3x3 convolutions on the
+// N x N grid of the 2-D operator, 32 channels, BF16 weights and activations,
+// FP32 accumulation, zero padding at the grid boundary.
+//
+//   z_l = conv3x3(a_{l-1}; W_l) + b_l,  a_l = relu(z_l) (l < L),  out = z_L
+//
+// Activations are channel-last (image, y, x, 32 channels): 64 bytes a pixel.
+// Weights W_l[tap][c_in][c_out], tap = 3*dy + dx for the offset (dy-1, dx-1).
+//
+// k_conv3x3_tc: the convolution as an implicit GEMM on the tensor cores.
+// A CTA of 128 threads takes tiles of 128 consecutive pixels; per tile
+//   D (128 pixels x 32 out-channels, FP32, in tensor memory)
+//     = A (128 x 288: the nine shifted 32-channel neighbours of each pixel)
+//     x B (288 x 32: the weights),
+// with A and B in shared memory in the canonical no-swizzle K-major layout
+// (8-row x 16-byte core matrices; LBO = 128 B between core matrices along K,
+// SBO = 36 * 128 B between 8-row groups), issued as 18 tcgen05.mma
+// (M = 128, N = 32, K = 16, kind::f16 with BF16 operands) by one thread and
+// committed to an mbarrier; every warp then reads its 32 rows of D with
+// tcgen05.ld and applies the epilogue (bias, ReLU, or the ReLU mask of the
+// backward pass) before storing BF16 (and optionally FP32) results.
+// The backward data pass is the same kernel with the weights flipped and
+// their channel axes swapped; the weight gradient is a CUDA-core reduction
+// over pixels (per-CTA partials, fixed-order sum).
+#include <cuda_bf16.h>
+#include "kernels.h"
+
+namespace {
+
+constexpr int kC = 32;               // channels
+constexpr int kK = 9 * kC;           // GEMM depth: 288
+constexpr int kTile = 128;           // pixels per tile (GEMM M)
+constexpr int kLBO = 128;            // bytes between core matrices along K
+constexpr int kSBO = (kK / 8) * 128; // bytes between 8-row groups: 4608
+constexpr int kAB = kTile * kK * 2;  // A tile bytes: 73728
+constexpr int kBB = kC * kK * 2;     // weight bytes: 18432
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading and
+// stride byte offsets (all >> 4), fixed bits 46..48 = 0b001, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at
+// bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kC >> 3) << 17) |
+                            ((uint32_t)(kTile >> 4) << 24);
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+// Bounded wait on an mbarrier phase; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase) {
+  const uint32_t a = smem_u32(bar);
+  for (long long it = 0; it < (1ll << 26); ++it) {
+    uint32_t done = 0;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(phase)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float *v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// byte offset of element (row, k) in a canonical K-major no-swizzle operand
+__device__ __forceinline__ int canon_off(int row, int k) {
+  return (row >> 3) * kSBO + (k >> 3) * kLBO + (row & 7) * 16 + (k & 7) * 2;
+}
+
+}  // namespace
+
+// out[p][co] = epilogue(sum_{tap, ci} W[tap][ci][co] in[p + off(tap)][ci])
+// epilogue: + bias[co] (if bias), relu (if relu), * (mask[p][co] > 0) (if mask);
+// stored as BF16 to out (if out) and FP32 to outf (if outf).
+__global__ void __launch_bounds__(128, 2) k_conv3x3_tc(const __nv_bfloat16 *__restrict__ in,
+                                                       const __nv_bfloat16 *__restrict__ W,
+                                                       const float *__restrict__ bias,
+                                                       const __nv_bfloat16 *__restrict__ mask, int relu,
+                                                       __nv_bfloat16 *__restrict__ out, float *__restrict__ outf,
+                                                       int nimg, int N, int *err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char *As = smem;
+  unsigned char *Bs = smem + kAB;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kAB + kBB);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + kAB + kBB + 16);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // weights -> canonical B layout (row = out-channel n, k = tap*32 + ci)
+  for (int e = tid; e < kK * (kC / 8); e += blockDim.x) {
+    const int k = e / (kC / 8), n8 = (e % (kC / 8)) * 8;  // 8 consecutive out-channels of one k
+    const int tap = k / kC, ci = k % kC;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const __nv_bfloat16 v = W[((size_t)tap * kC + ci) * kC + n8 + q];
+      *reinterpret_cast<__nv_bfloat16 *>(Bs + canon_off(n8 + q, k)) = v;
+    }
+  }
+  if (tid == 0) mbar_init(bar, 1);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const long long npix = (long long)nimg * N * N;
+  const long long ntiles = (npix + kTile - 1) / kTile;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    // ---- im2col of this thread's pixel into the canonical A layout ----
+    const long long p = t * kTile + tid;
+    int img = 0, y = 0, x = 0;
+    const bool live = p < npix;
+    if (live) {
+      img = (int)(p / ((long long)N * N));
+      const int rem = (int)(p - (long long)img * N * N);
+      y = rem / N;
+      x = rem - y * N;
+    }
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+      const bool inb = live && yy >= 0 && yy < N && xx >= 0 && xx < N;
+      const uint4 *src = reinterpret_cast<const uint4 *>(in + (((size_t)img * N + (inb ? yy : 0)) * N +
+                                                               (inb ? xx : 0)) * kC);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint4 v = inb ? src[q] : make_uint4(0, 0, 0, 0);
+        *reinterpret_cast<uint4 *>(As + canon_off(tid, tap * kC + q * 8)) = v;
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    // ---- 18 MMAs, K = 16 each ----
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+#pragma unroll
+      for (int s = 0; s < kK / 16; ++s)
+        tc_mma(tmem, smem_desc(a0 + s * 2 * kLBO, kLBO, kSBO), smem_desc(b0 + s * 2 * kLBO, kLBO, kSBO), s > 0);
+      tc_commit(bar);
+    }
+    // the CTA agrees on the outcome of the bounded wait, so that every thread
+    // takes the same path through the barriers below
+    const bool waited = mbar_wait(bar, phase);
+    if (__syncthreads_or(!waited)) {
+      if (tid == 0) atomicOr(err, DEVERR_TIMEOUT);
+      ok = false;
+    }
+    phase ^= 1;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // ---- epilogue: warp w holds rows (pixels) 32w .. 32w+31 ----
+    float v[32];
+    tc_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
+    if (live) {
+      if (bias) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] += bias[k];
+      }
+      if (relu) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = fmaxf(v[k], 0.f);
+      }
+      if (mask) {
+        const __nv_bfloat16 *mk_ = mask + (size_t)p * kC;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = __bfloat162float(mk_[k]) > 0.f ? v[k] : 0.f;
+      }
+      if (out) {
+        uint4 *dst = reinterpret_cast<uint4 *>(out + (size_t)p * kC);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          __nv_bfloat162 h[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) h[u] = __floats2bfloat162_rn(v[q * 8 + 2 * u], v[q * 8 + 2 * u + 1]);
+          dst[q] = *reinterpret_cast<uint4 *>(h);
+        }
+      }
+      if (outf) {
+        float4 *dst = reinterpret_cast<float4 *>(outf + (size_t)p * kC);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
+}
+
+// Weights of the adjoint convolution: Wt[tap'][co][ci] = W[tap][ci][co] with
+// tap' the mirrored tap (offset negated).
+__global__ void k_conv_adjoint_weights(const __nv_bfloat16 *W, __nv_bfloat16 *Wt) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 9 * kC * kC; e += gridDim.x * blockDim.x) {
+    const int tap = e / (kC * kC), ci = (e / kC) % kC, co = e % kC;
+    Wt[((size_t)(8 - tap) * kC + co) * kC + ci] = W[e];
+  }
+}
+
+// Weight and bias gradients of one layer: dW[tap][ci][co] = sum_p
+// a[p + off(tap)][ci] g[p][co], db[co] = sum_p g[p][co].  Each CTA reduces a
+// contiguous chunk of pixels into its own partial (thread = (tap, ci), 32
+// accumulators); k_net_reduce sums the partials in CTA order.
+constexpr int kGradPix = 64;
+__global__ void __launch_bounds__(288) k_conv_wgrad(const __nv_bfloat16 *__restrict__ a,
+                                                    const __nv_bfloat16 *__restrict__ g, int nimg, int N,
+                                                    long long pix_per_cta, float *__restrict__ part) {
+  __shared__ float gs[kGradPix][kC];
+  const int tid = threadIdx.x;  // tid = tap * 32 + ci
+  const int tap = tid / kC, ci = tid % kC;
+  const long long npix = (long long)nimg * N * N;
+  const long long p0 = blockIdx.x * pix_per_cta, p1 = min(npix, p0 + pix_per_cta);
+  float acc[kC];
+#pragma unroll
+  for (int k = 0; k < kC; ++k) acc[k] = 0.f;
+  float bacc = 0.f;
+  for (long long pb = p0; pb < p1; pb += kGradPix) {
+    const int cnt = (int)min((long long)kGradPix, p1 - pb);
+    __syncthreads();
+    for (int e = tid; e < kGradPix * kC; e += blockDim.x) {
+      const int r = e / kC, c = e % kC;
+      gs[r][c] = r < cnt ? __bfloat162float(g[(size_t)(pb + r) * kC + c]) : 0.f;
+    }
+    __syncthreads();
+    for (int r = 0; r < cnt; ++r) {
+      const long long p = pb + r;
+      const int img = (int)(p / ((long long)N * N));
+      const int rem = (int)(p - (long long)img * N * N);
+      const int y = rem / N, x = rem - (rem / N) * N;
+      const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+      if (yy < 0 || yy >= N || xx < 0 || xx >= N) continue;
+      const float av = __bfloat162float(a[(((size_t)img * N + yy) * N + xx) * kC + ci]);
+#pragma unroll
+      for (int k = 0; k < kC; ++k) acc[k] = fmaf(av, gs[r][k], acc[k]);
+    }
+    if (tid < kC)
+      for (int r = 0; r < cnt; ++r) bacc += gs[r][tid];
+  }
+  float *o = part + (size_t)blockIdx.x * (9 * kC * kC + kC);
+#pragma unroll
+  for (int k = 0; k < kC; ++k) o[(size_t)tid * kC + k] = acc[k];
+  if (tid < kC) o[9 * kC * kC + tid] = bacc;
+}
+
+__global__ void k_net_reduce(const float *part, int nparts, int count, float *out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int p = 0; p < nparts; ++p) s += part[(size_t)p * count + e];
+    out[e] = (float)s;
+  }
+}
+
+// Loss of the first cout channels against the FP32 target and its gradient
+// g = 2 (out - t) / count as BF16 (other channels zero); loss summed in FP64.
+__global__ void k_net_loss_grad(const float *__restrict__ out, const float *__restrict__ target, int cout,
+                                long long npix, __nv_bfloat16 *__restrict__ g, double *loss) {
+  double local = 0.0;
+  const double inv = 1.0 / ((double)npix * cout);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < npix * kC;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long p = e / kC;
+    const int c = (int)(e - p * kC);
+    float gv = 0.f;
+    if (c < cout) {
+      const float d = out[e] - target[p * cout + c];
+      local += (double)d * d;
+      gv = (float)(2.0 * d * inv);
+    }
+    g[e] = __float2bfloat16(gv);
+  }
+  for (int o = 16; o; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, local * inv);
+}
+
+// Adam step on FP32 master parameters; BF16 copy of the weights for the
+// convolution kernel.  t: step number (1-based).
+__global__ void k_net_adam(float *w, const float *grad, float *m1, float *m2, int count, float lr, float b1,
+                           float b2, float epsv, int t, __nv_bfloat16 *wb, int nweights) {
+  const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
+    const float gr = grad[e];
+    m1[e] = b1 * m1[e] + (1.f - b1) * gr;
+    m2[e] = b2 * m2[e] + (1.f - b2) * gr * gr;
+    w[e] -= lr * (m1[e] / c1) / (sqrtf(m2[e] / c2) + epsv);
+    if (e < nweights) wb[e] = __float2bfloat16(w[e]);
+  }
+}
+
+__global__ void k_to_bf16(const float *x, __nv_bfloat16 *y, long long count) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count; e += (long long)gridDim.x * blockDim.x)
+    y[e] = __float2bfloat16(x[e]);
+}
+__global__ void k_bf16_to_f32(const __nv_bfloat16 *x, float *y, long long count) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count; e += (long long)gridDim.x * blockDim.x)
+    y[e] = __bfloat162float(x[e]);
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+size_t conv_tc_smem_bytes() { return (size_t)kAB + kBB + 64; }
+
+cudaError_t launch_conv3x3_tc(const void *in, const void *W, const float *bias, const void *mask, int relu, void *out,
+                              float *outf, int nimg, int N, int *err, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_conv3x3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)conv_tc_smem_bytes());
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long ntiles = ((long long)nimg * N * N + kTile - 1) / kTile;
+  long long g = (long long)sms * 2;
+  if (g > ntiles) g = ntiles;
+  if (g < 1) g = 1;
+  k_conv3x3_tc<<<(unsigned)g, kTile, conv_tc_smem_bytes(), s>>>(
+      (const __nv_bfloat16 *)in, (const __nv_bfloat16 *)W, bias, (const __nv_bfloat16 *)mask, relu,
+      (__nv_bfloat16 *)out, outf, nimg, N, err);
+  note_launch();
+  return cudaGetLastError();
+}
+
+void launch_conv_adjoint_weights(const void *W, void *Wt, cudaStream_t s) {
+  k_conv_adjoint_weights<<<ceil_div(9 * kC * kC, 256), 256, 0, s>>>((const __nv_bfloat16 *)W, (__nv_bfloat16 *)Wt);
+  note_launch();
+}
+
+int conv_wgrad_parts(long long npix) {
+  long long p = (npix + 4095) / 4096;
+  if (p > 1216) p = 1216;
+  return (int)(p < 1 ? 1 : p);
+}
+
+void launch_conv_wgrad(const void *a, const void *g, int nimg, int N, float *part, float *dWb, cudaStream_t s) {
+  const long long npix = (long long)nimg * N * N;
+  const int parts = conv_wgrad_parts(npix);
+  const long long per = (npix + parts - 1) / parts;
+  k_conv_wgrad<<<parts, 288, 0, s>>>((const __nv_bfloat16 *)a, (const __nv_bfloat16 *)g, nimg, N, per, part);
+  note_launch();
+  const int count = 9 * kC * kC + kC;
+  k_net_reduce<<<ceil_div(count, 256), 256, 0, s>>>(part, parts, count, dWb);
+  note_launch();
+}
+
+void launch_net_loss_grad(const float *out, const float *target, int cout, long long npix, void *g, double *loss,
+                          cudaStream_t s) {
+  k_net_loss_grad<<<grid_for((size_t)npix * kC), 256, 0, s>>>(out, target, cout, npix, (__nv_bfloat16 *)g, loss);
+  note_launch();
+}
+
+void launch_net_adam(float *w, const float *grad, float *m1, float *m2, int count, float lr, int t, void *wb,
+                     int nweights, cudaStream_t s) {
+  k_net_adam<<<ceil_div(count, 256), 256, 0, s>>>(w, grad, m1, m2, count, lr, 0.9f, 0.999f, 1e-8f, t,
+                                                  (__nv_bfloat16 *)wb, nweights);
+  note_launch();
+}
+
+void launch_to_bf16(const float *x, void *y, long long count, cudaStream_t s) {
+  k_to_bf16<<<grid_for((size_t)count), 256, 0, s>>>(x, (__nv_bfloat16 *)y, count);
+  note_launch();
+}
+void launch_bf16_to_f32(const void *x, float *y, long long count, cudaStream_t s) {
+  k_bf16_to_f32<<<grid_for((size_t)count), 256, 0, s>>>((const __nv_bfloat16 *)x, y, count);
+  note_launch();
+}
+
+// ---------------------------------------------------------------------------
+// network object (C ABI in feast_nh.h)
+// ---------------------------------------------------------------------------
+#include <string>
+#include <vector>
+#include "feast_nh.h"
+
+struct feast_nh_net {
+  int L = 0, N = 0, maxi = 0, t = 0;
+  cudaStream_t s = nullptr;
+  std::vector<void *> allocs;
+  float *params = nullptr, *grad = nullptr, *m1 = nullptr, *m2 = nullptr;
+  __nv_bfloat16 *wb = nullptr, *wt = nullptr;
+  std::vector<__nv_bfloat16 *> act;  // act[0]: input, act[l]: output of layer l - 1
+  float *outf = nullptr;
+  __nv_bfloat16 *g0 = nullptr, *g1 = nullptr;
+  float *wpart = nullptr;
+  double *dloss = nullptr;
+  int *derr = nullptr;
+  std::string err;
+};
+
+namespace {
+constexpr int kLayerP = 9 * kC * kC + kC;  // parameters per layer: W then b
+constexpr int kLayerW = 9 * kC * kC;
+
+template <typename P>
+P *nalloc(feast_nh_net *n, size_t bytes, bool &ok) {
+  void *p = nullptr;
+  if (!ok) return nullptr;
+  if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) {
+    ok = false;
+    return nullptr;
+  }
+  n->allocs.push_back(p);
+  return reinterpret_cast<P *>(p);
+}
+
+void net_free(feast_nh_net *n) {
+  if (!n) return;
+  if (n->s) cudaStreamSynchronize(n->s);
+  for (void *p : n->allocs) cudaFree(p);
+  delete n;
+}
+
+feast_nh_status net_forward(feast_nh_net *n, int nimg) {
+  for (int l = 0; l < n->L; ++l) {
+    const bool last = l == n->L - 1;
+    const cudaError_t e =
+        launch_conv3x3_tc(n->act[l], n->wb + (size_t)l * kLayerW, n->params + (size_t)l * kLayerP + kLayerW, nullptr,
+                          last ? 0 : 1, last ? nullptr : n->act[l + 1], last ? n->outf : nullptr, nimg, n->N, n->derr,
+                          n->s);
+    if (e != cudaSuccess) {
+      n->err = std::string("network forward: ") + cudaGetErrorString(e);
+      return FEAST_NH_ECUDA;
+    }
+  }
+  return FEAST_NH_OK;
+}
+
+feast_nh_status net_check(feast_nh_net *n) {
+  int herr = 0;
+  if (cudaMemcpyAsync(&herr, n->derr, sizeof(int), cudaMemcpyDeviceToHost, n->s) != cudaSuccess ||
+      cudaStreamSynchronize(n->s) != cudaSuccess) {
+    n->err = "network: CUDA error";
+    return FEAST_NH_ECUDA;
+  }
+  if (herr & DEVERR_TIMEOUT) {
+    n->err = "network: a bounded wait for the tensor-core product gave up";
+    return FEAST_NH_ETIMEOUT;
+  }
+  return FEAST_NH_OK;
+}
+}  // namespace
+
+// forward of the network on nimg bf16 channel-last images already in act[0]
+// (used by the preconditioned Krylov solver)
+feast_nh_status net_apply_internal(feast_nh_net *n, int nimg, const float **out) {
+  if (nimg > n->maxi) return FEAST_NH_EINVAL;
+  const feast_nh_status st = net_forward(n, nimg);
+  *out = n->outf;
+  return st;
+}
+void *net_input_buffer(feast_nh_net *n) { return n->act[0]; }
+int net_grid(const feast_nh_net *n) { return n->N; }
+int net_max_images(const feast_nh_net *n) { return n->maxi; }
+
+extern "C" {
+
+feast_nh_status feast_nh_net_create(feast_nh_net **out, int32_t layers, int32_t N, int32_t max_images,
+                                    void *stream) {
+  if (!out) return FEAST_NH_EINVAL;
+  *out = nullptr;
+  if (layers < 1 || layers > 16 || N < 2 || max_images < 1) return FEAST_NH_EINVAL;
+  feast_nh_net *n = new feast_nh_net();
+  n->L = layers;
+  n->N = N;
+  n->maxi = max_images;
+  n->s = reinterpret_cast<cudaStream_t>(stream);
+  bool ok = true;
+  const size_t np = (size_t)layers * kLayerP;
+  const size_t pix = (size_t)max_images * N * N;
+  n->params = nalloc<float>(n, np * sizeof(float), ok);
+  n->grad = nalloc<float>(n, np * sizeof(float), ok);
+  n->m1 = nalloc<float>(n, np * sizeof(float), ok);
+  n->m2 = nalloc<float>(n, np * sizeof(float), ok);
+  n->wb = nalloc<__nv_bfloat16>(n, (size_t)layers * kLayerW * 2, ok);
+  n->wt = nalloc<__nv_bfloat16>(n, (size_t)kLayerW * 2, ok);
+  n->act.assign(layers, nullptr);
+  for (int l = 0; l < layers; ++l) n->act[l] = nalloc<__nv_bfloat16>(n, pix * kC * 2, ok);
+  n->outf = nalloc<float>(n, pix * kC * sizeof(float), ok);
+  n->g0 = nalloc<__nv_bfloat16>(n, pix * kC * 2, ok);
+  n->g1 = nalloc<__nv_bfloat16>(n, pix * kC * 2, ok);
+  n->wpart = nalloc<float>(n, (size_t)conv_wgrad_parts((long long)pix) * kLayerP * sizeof(float), ok);
+  n->dloss = nalloc<double>(n, sizeof(double), ok);
+  n->derr = nalloc<int>(n, sizeof(int), ok);
+  if (!ok) {
+    net_free(n);
+    return FEAST_NH_ENOMEM;
+  }
+  if (cudaMemsetAsync(n->params, 0, np * sizeof(float), n->s) != cudaSuccess ||
+      cudaMemsetAsync(n->m1, 0, np * sizeof(float), n->s) != cudaSuccess ||
+      cudaMemsetAsync(n->m2, 0, np * sizeof(float), n->s) != cudaSuccess ||
+      cudaMemsetAsync(n->wb, 0, (size_t)layers * kLayerW * 2, n->s) != cudaSuccess ||
+      cudaMemsetAsync(n->derr, 0, sizeof(int), n->s) != cudaSuccess ||
+      cudaStreamSynchronize(n->s) != cudaSuccess) {
+    net_free(n);
+    return FEAST_NH_ECUDA;
+  }
+  *out = n;
+  return FEAST_NH_OK;
+}
+
+void feast_nh_net_destroy(feast_nh_net *n) { net_free(n); }
+
+const char *feast_nh_net_last_error(const feast_nh_net *n) { return n ? n->err.c_str() : ""; }
+
+feast_nh_status feast_nh_net_set_params(feast_nh_net *n, const float *params) {
+  if (!n || !params) return FEAST_NH_EINVAL;
+  const size_t np = (size_t)n->L * kLayerP;
+  if (cudaMemcpyAsync(n->params, params, np * sizeof(float), cudaMemcpyHostToDevice, n->s) != cudaSuccess)
+    return FEAST_NH_ECUDA;
+  for (int l = 0; l < n->L; ++l)
+    launch_to_bf16(n->params + (size_t)l * kLayerP, n->wb + (size_t)l * kLayerW, kLayerW, n->s);
+  cudaMemsetAsync(n->m1, 0, np * sizeof(float), n->s);
+  cudaMemsetAsync(n->m2, 0, np * sizeof(float), n->s);
+  n->t = 0;
+  return cudaStreamSynchronize(n->s) == cudaSuccess ? FEAST_NH_OK : FEAST_NH_ECUDA;
+}
+
+feast_nh_status feast_nh_net_get_params(feast_nh_net *n, float *params) {
+  if (!n || !params) return FEAST_NH_EINVAL;
+  if (cudaMemcpyAsync(params, n->params, (size_t)n->L * kLayerP * sizeof(float), cudaMemcpyDeviceToHost, n->s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(n->s) != cudaSuccess)
+    return FEAST_NH_ECUDA;
+  return FEAST_NH_OK;
+}
+
+feast_nh_status feast_nh_net_forward(feast_nh_net *n, const float *x, float *out, int32_t nimg) {
+  if (!n || !x || !out || nimg < 1 || nimg > n->maxi) return FEAST_NH_EINVAL;
+  const long long cnt = (long long)nimg * n->N * n->N * kC;
+  cudaMemsetAsync(n->derr, 0, sizeof(int), n->s);
+  launch_to_bf16(x, n->act[0], cnt, n->s);
+  feast_nh_status st = net_forward(n, nimg);
+  if (st != FEAST_NH_OK) return st;
+  if (cudaMemcpyAsync(out, n->outf, cnt * sizeof(float), cudaMemcpyDeviceToDevice, n->s) != cudaSuccess)
+    return FEAST_NH_ECUDA;
+  return net_check(n);
+}
+
+feast_nh_status feast_nh_net_train_step(feast_nh_net *n, const float *x, const float *target, int32_t cout,
+                                        int32_t nimg, float lr, double *loss, float *grad_out) {
+  if (!n || !x || !target || cout < 1 || cout > kC || nimg < 1 || nimg > n->maxi || lr < 0) return FEAST_NH_EINVAL;
+  cudaStream_t s = n->s;
+  const long long npix = (long long)nimg * n->N * n->N;
+  cudaMemsetAsync(n->derr, 0, sizeof(int), s);
+  cudaMemsetAsync(n->dloss, 0, sizeof(double), s);
+  launch_to_bf16(x, n->act[0], npix * kC, s);
+  feast_nh_status st = net_forward(n, nimg);
+  if (st != FEAST_NH_OK) return st;
+  launch_net_loss_grad(n->outf, target, cout, npix, n->g0, n->dloss, s);
+  __nv_bfloat16 *g = n->g0, *gn = n->g1;
+  for (int l = n->L - 1; l >= 0; --l) {
+    launch_conv_wgrad(n->act[l], g, nimg, n->N, n->wpart, n->grad + (size_t)l * kLayerP, s);
+    if (l > 0) {
+      // gradient of the layer's input, masked by relu' of the layer below
+      launch_conv_adjoint_weights(n->wb + (size_t)l * kLayerW, n->wt, s);
+      const cudaError_t e = launch_conv3x3_tc(g, n->wt, nullptr, n->act[l], 0, gn, nullptr, nimg, n->N, n->derr, s);
+      if (e != cudaSuccess) {
+        n->err = std::string("network backward: ") + cudaGetErrorString(e);
+        return FEAST_NH_ECUDA;
+      }
+      std::swap(g, gn);
+    }
+  }
+  if (grad_out &&
+      cudaMemcpyAsync(grad_out, n->grad, (size_t)n->L * kLayerP * sizeof(float), cudaMemcpyDeviceToDevice, s) !=
+          cudaSuccess)
+    return FEAST_NH_ECUDA;
+  if (lr > 0) {
+    ++n->t;
+    for (int l = 0; l < n->L; ++l)
+      launch_net_adam(n->params + (size_t)l * kLayerP, n->grad + (size_t)l * kLayerP, n->m1 + (size_t)l * kLayerP,
+                      n->m2 + (size_t)l * kLayerP, kLayerP, lr, n->t, n->wb + (size_t)l * kLayerW, kLayerW, s);
+  }
+  if (loss && cudaMemcpyAsync(loss, n->dloss, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return FEAST_NH_ECUDA;
+  return net_check(n);
+}
+
+}  // extern "C"

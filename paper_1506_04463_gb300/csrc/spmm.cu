@@ -526,9 +526,23 @@ __global__ void __launch_bounds__(256) k_multishift_spmm_f32(CsrView A, CsrView 
   }
 }
 
-int launch_multishift_spmm_f32(const CsrView &A, const CsrView *B, int ne, const cxd *d_z, int conj_z, const cxf *P,
-                               cxf *V, int m, int grid_per_sm, cudaStream_t s) {
-  constexpr int KMAX = 8;
+// Longest row of a CSR matrix (entries), for the register row length of the
+// FP32 operator.
+__global__ void k_max_row_nnz(CsrView A, int *out) {
+  int mx = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x)
+    mx = max(mx, (int)(A.rowptr[i + 1] - A.rowptr[i]));
+  for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
+}
+void launch_max_row_nnz(const CsrView &A, int *d_out, cudaStream_t s) {
+  k_max_row_nnz<<<min(1024, ceil_div(A.n, 256)), 256, 0, s>>>(A, d_out);
+  note_launch();
+}
+
+template <int KMAX>
+static long long spmm_f32_dispatch(const CsrView &A, const CsrView *B, int ne, const cxd *d_z, int conj_z,
+                                   const cxf *P, cxf *V, int m, int grid_per_sm, cudaStream_t s) {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -562,6 +576,18 @@ int launch_multishift_spmm_f32(const CsrView &A, const CsrView *B, int ne, const
   }
 #undef SPF_VW
 #undef SPF
+  return g;
+}
+
+int launch_multishift_spmm_f32(const CsrView &A, const CsrView *B, int ne, const cxd *d_z, int conj_z, const cxf *P,
+                               cxf *V, int m, int grid_per_sm, int max_row_nnz, cudaStream_t s) {
+  // register row length: the smallest that holds the longest row (longer
+  // rows and a non-identity B take the general loop of the same kernel)
+  long long g;
+  if (max_row_nnz <= 5) g = spmm_f32_dispatch<5>(A, B, ne, d_z, conj_z, P, V, m, grid_per_sm, s);
+  else if (max_row_nnz <= 7) g = spmm_f32_dispatch<7>(A, B, ne, d_z, conj_z, P, V, m, grid_per_sm, s);
+  else if (max_row_nnz <= 9) g = spmm_f32_dispatch<9>(A, B, ne, d_z, conj_z, P, V, m, grid_per_sm, s);
+  else g = spmm_f32_dispatch<16>(A, B, ne, d_z, conj_z, P, V, m, grid_per_sm, s);
   note_launch();
   return (int)g;
 }

@@ -69,7 +69,9 @@ EXPORTS = ["feast_nh_default_opts", "feast_nh_init", "feast_nh_filter", "feast_n
            "feast_nh_destroy", "feast_nh_strerror", "feast_nh_last_error", "feast_nh_nodes",
            "feast_nh_multishift_residual", "feast_nh_kernel_launches", "feast_nh_multishift_residual_noalloc",
            "feast_nh_small_eig", "feast_nh_inject_device_error", "feast_nh_batch_init", "feast_nh_batch_solve",
-           "feast_nh_batch_destroy", "feast_nh_batch_last_error", "feast_nh_multishift_spmm"]
+           "feast_nh_batch_destroy", "feast_nh_batch_last_error", "feast_nh_multishift_spmm", "feast_nh_net_create",
+           "feast_nh_net_set_params", "feast_nh_net_get_params", "feast_nh_net_forward", "feast_nh_net_train_step",
+           "feast_nh_net_destroy", "feast_nh_net_last_error"]
 
 _lib = None
 
@@ -114,6 +116,18 @@ def lib():
     L.feast_nh_batch_destroy.restype = None
     L.feast_nh_batch_last_error.argtypes = [vp]
     L.feast_nh_batch_last_error.restype = C.c_char_p
+    L.feast_nh_net_create.argtypes = [C.POINTER(vp), i32, i32, i32, vp]
+    L.feast_nh_net_set_params.argtypes = [vp, C.POINTER(C.c_float)]
+    L.feast_nh_net_get_params.argtypes = [vp, C.POINTER(C.c_float)]
+    L.feast_nh_net_forward.argtypes = [vp, vp, vp, i32]
+    L.feast_nh_net_train_step.argtypes = [vp, vp, vp, i32, i32, C.c_float, C.POINTER(C.c_double), vp]
+    L.feast_nh_net_destroy.argtypes = [vp]
+    L.feast_nh_net_destroy.restype = None
+    L.feast_nh_net_last_error.argtypes = [vp]
+    L.feast_nh_net_last_error.restype = C.c_char_p
+    for f in ("feast_nh_net_create", "feast_nh_net_set_params", "feast_nh_net_get_params", "feast_nh_net_forward",
+              "feast_nh_net_train_step"):
+        getattr(L, f).restype = i32
     L.feast_nh_kernel_launches.argtypes = []
     L.feast_nh_kernel_launches.restype = C.c_uint64
     for f in ("feast_nh_init", "feast_nh_filter", "feast_nh_rr", "feast_nh_solve", "feast_nh_nodes",
@@ -419,6 +433,69 @@ class FeastBatch:
     def close(self):
         if getattr(self, "h", None):
             lib().feast_nh_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+NET_CH = 32
+NET_LAYER_PARAMS = 9 * NET_CH * NET_CH + NET_CH
+
+
+class Net:
+    """The learned preconditioner's network (feast_nh_net_* of the C ABI):
+    `layers` 3x3 convolutions, 32 channels, on an N x N grid."""
+
+    def __init__(self, layers, N, max_images, device="cuda", stream=None):
+        self.layers, self.N, self.max_images = int(layers), int(N), int(max_images)
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = C.c_void_p()
+        st = lib().feast_nh_net_create(C.byref(h), self.layers, self.N, self.max_images,
+                                       C.c_void_p(self.stream.cuda_stream))
+        if st != OK:
+            raise FeastError(st, "feast_nh_net_create")
+        self.h = h
+
+    def _check(self, st, what):
+        if st != OK:
+            raise FeastError(st, f"{what}: {lib().feast_nh_net_last_error(self.h).decode()}")
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(np.asarray(params, np.float32).ravel())
+        assert p.size == self.layers * NET_LAYER_PARAMS
+        self._check(lib().feast_nh_net_set_params(self.h, p.ctypes.data_as(C.POINTER(C.c_float))), "set_params")
+
+    def get_params(self):
+        p = np.zeros(self.layers * NET_LAYER_PARAMS, np.float32)
+        self._check(lib().feast_nh_net_get_params(self.h, p.ctypes.data_as(C.POINTER(C.c_float))), "get_params")
+        return p
+
+    def forward(self, x):
+        """x: (nimg, N, N, 32) float32 device tensor -> same shape."""
+        x = x.contiguous()
+        out = torch.empty_like(x)
+        self._check(lib().feast_nh_net_forward(self.h, _ptr(x), _ptr(out), x.shape[0]), "forward")
+        return out
+
+    def train_step(self, x, target, lr, want_grad=False):
+        """One step on the MSE of the first target.shape[-1] channels; returns
+        (loss, gradient or None)."""
+        x, target = x.contiguous(), target.contiguous()
+        loss = C.c_double()
+        grad = torch.empty(self.layers * NET_LAYER_PARAMS, dtype=torch.float32, device=self.device) \
+            if want_grad else None
+        self._check(lib().feast_nh_net_train_step(self.h, _ptr(x), _ptr(target), target.shape[-1], x.shape[0],
+                                                  float(lr), C.byref(loss), _ptr(grad)), "train_step")
+        return loss.value, grad
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().feast_nh_net_destroy(self.h)
             self.h = None
 
     def __del__(self):

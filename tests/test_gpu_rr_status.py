@@ -192,3 +192,20 @@ def test_injected_device_error_maps_to_status(bits, status):
     again = ctx.solve(dev(wk.Y0), dev(wk.Yh0))
     assert again["status"] == F.OK and torch.equal(again["lam"], ref["lam"])
     ctx.close()
+
+
+@pytest.mark.parametrize("defect", ["column", "rowptr"])
+def test_malformed_csr_rejected(defect):
+    # column indices and row pointers are validated before any kernel
+    # scatters through them: a bad CSR is EINVAL, not a fault
+    wk = banded_workload(n=120, kl=2, ku=2, m0=6, ne=4, with_b=False)
+    rp, ci, val, dt, n, nnz = F.csr_to_device(wk.A)
+    if defect == "column":
+        ci = ci.clone()
+        ci[17] = n                      # one index past the last column
+    else:
+        rp = rp.clone()
+        rp[40] = rp[42] + 1             # row pointers decrease
+    with pytest.raises(F.FeastError) as e:
+        F.FeastNH((rp, ci, val, dt, n, nnz), None, wk.contour, 6)
+    assert e.value.status == F.EINVAL
