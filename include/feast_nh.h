@@ -77,7 +77,8 @@ typedef struct {
   const double *z, *w;
 } feast_nh_contour;
 
-enum { FEAST_NH_INNER_BANDED = 0, FEAST_NH_INNER_BICGSTAB = 1 };
+enum { FEAST_NH_INNER_BANDED = 0, FEAST_NH_INNER_BICGSTAB = 1, FEAST_NH_INNER_FGMRES = 2 };
+enum { FEAST_NH_PRECOND_NONE = 0, FEAST_NH_PRECOND_JACOBI = 1, FEAST_NH_PRECOND_LEARNED = 2 };
 enum { FEAST_NH_PREC_FP64 = 0, FEAST_NH_PREC_FP32_IR = 1 };
 enum { FEAST_NH_PROBLEM_GENERAL = 0, FEAST_NH_PROBLEM_COMPLEX_SYMMETRIC = 1 };
 
@@ -97,8 +98,11 @@ typedef struct {
   int32_t problem;    /* FEAST_NH_PROBLEM_GENERAL */
   int32_t timing;     /* 1: record CUDA events around the banded solve and
                          multi-shift kernels; totals go to feast_nh_info   */
-  int32_t krylov_max; /* 1000: Krylov iterations per refinement step of the
-                         batched solver (feast_nh_batch_*)                  */
+  int32_t krylov_max; /* 1000: Krylov iterations per refinement step (batched
+                         solver and FGMRES)                                 */
+  int32_t krylov_restart; /* 30: FGMRES restart length (<= 64)              */
+  int32_t precond;    /* FGMRES right preconditioner: FEAST_NH_PRECOND_JACOBI
+                         (default), _NONE, or _LEARNED (feast_nh_set_network) */
 } feast_nh_opts;
 
 /* Per-call record (host).  Times are CUDA-event milliseconds on the stream. */
@@ -128,7 +132,16 @@ typedef struct {
                                the banded factors (no pivoting is done: a
                                tiny ratio flags factors that may be
                                inaccurate; the refinement residual decides)   */
+  int32_t krylov_iterations; /* FGMRES iterations summed over the sides,
+                               refinement steps and filters of the call       */
 } feast_nh_info;
+
+/* inner_kind FEAST_NH_INNER_FGMRES (with precision FEAST_NH_PREC_FP32_IR):
+ * the shifted systems are solved by restarted flexible GMRES in complex FP32
+ * over every (node, column) system at once, right-preconditioned by
+ * opts.precond, inside FP64 iterative refinement (each refinement step asks
+ * FGMRES for a relative reduction of max(1e-5, inner_tol), at most
+ * krylov_max iterations; the FP64 residual decides convergence). */
 
 /* Fills *o with the defaults listed above. */
 void feast_nh_default_opts(feast_nh_opts *o);
@@ -174,6 +187,39 @@ feast_nh_status feast_nh_rr(feast_nh_ctx *ctx, const void *Q, const void *Qh, in
  * still reports the count). */
 feast_nh_status feast_nh_solve(feast_nh_ctx *ctx, const void *Y0, const void *Yh0, double *lambda,
                                void *X, void *Xh, double *res, int32_t *m_found, feast_nh_info *info);
+
+/* Attaches a trained network (feast_nh_net_*) as the right preconditioner of
+ * the FGMRES inner solver (opts.precond == FEAST_NH_PRECOND_LEARNED).  The
+ * operator must live on an N x N grid with n = N^2 (row i = y N + x, the
+ * network's image layout).  Input channels per system (node j, column c):
+ * Re v / rms(v), Im v / rms(v), kappa Re z_j, kappa Im z_j (conjugated for
+ * the ^H side), then the nfeat <= 28 constant features (host floats); the
+ * output channels 0, 1 scaled back by rms(v) are the preconditioned vector.
+ * The context does not own the network; it must outlive the context's
+ * filters. */
+struct feast_nh_net;
+/* Training pairs for the network from the method's own exact solves: with
+ * ctx's banded direct solver (refined to opts.inner_tol), X_j = (z_j B -
+ * A)^{-1} R for the n x m block R (device, complex double); for every system
+ * s = j*m + c, Xin[s] (N x N x 32 floats, device) is column c of R packed as
+ * the preconditioner packs its input (r / rms(r), kappa, features as in
+ * feast_nh_set_network) and T[s] (N x N x 2 floats, device) is X_j[:, c] /
+ * rms(R[:, c]), the exact correction of that normalised input.  Returns
+ * FEAST_NH_EINNER if the solves missed inner_tol. */
+feast_nh_status feast_nh_learned_pairs(feast_nh_ctx *ctx, const void *R, int32_t m, int32_t N, float kappa,
+                                      const float *features, int32_t nfeat, float *Xin, float *T);
+/* Operator-norm training loss of network outputs `out` (m*ne images, N x N x
+ * 32 floats, device, channels 0 and 1 the complex correction) against the
+ * exact corrections T (as from feast_nh_learned_pairs): for system s = j*m+c
+ *     y_s = (z_j I - A)(out_s - T_s)       (side 1: (conj z_j I - A^H)),
+ * loss = sum |y|^2 / (ne m n) (host), and d loss / d out into gout (device,
+ * same shape as out, channels 2..31 zero).  Since (z_j I - A) T_s is the
+ * input residual, this is the residual left by the network's correction:
+ * it weighs errors by the operator, not by their size. */
+feast_nh_status feast_nh_operator_loss(feast_nh_ctx *ctx, const float *out, const float *T, int32_t m, int32_t N,
+                                      int32_t side, float *gout, double *loss);
+feast_nh_status feast_nh_set_network(feast_nh_ctx *ctx, struct feast_nh_net *net, int32_t N, float kappa,
+                                     const float *features, int32_t nfeat);
 
 /* Number of CUDA kernels this library has launched in this process. */
 uint64_t feast_nh_kernel_launches(void);
@@ -348,6 +394,11 @@ feast_nh_status feast_nh_net_forward(feast_nh_net *net, const float *x, float *o
  * lr > 0 applies one Adam step (beta 0.9 / 0.999, eps 1e-8), lr = 0 none. */
 feast_nh_status feast_nh_net_train_step(feast_nh_net *net, const float *x, const float *target, int32_t cout,
                                         int32_t nimg, float lr, double *loss, float *grad);
+/* Backward pass from a given output gradient gout (nimg x N x N x 32,
+ * device) through the activations of the last feast_nh_net_forward call on
+ * the same images, parameter gradient into grad (device, may be NULL), one
+ * Adam step if lr > 0. */
+feast_nh_status feast_nh_net_backward(feast_nh_net *net, const float *gout, int32_t nimg, float lr, float *grad);
 void feast_nh_net_destroy(feast_nh_net *net);
 const char *feast_nh_net_last_error(const feast_nh_net *net);
 

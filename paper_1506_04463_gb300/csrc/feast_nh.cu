@@ -83,6 +83,15 @@ struct feast_nh_ctx {
   unsigned inject_bits = 0;   // host-requested device error bits (testing aid)
   bool rr_only = false;       // Rayleigh-Ritz workspace only (one problem of a batch)
   int max_nnz[2] = {0, 0};    // longest row of A and of A^H
+  void *fgwork = nullptr;     // FGMRES workspace
+  cxf *dfg = nullptr;         // FGMRES correction (node-major, complex float)
+  cxd *adiag = nullptr, *bdiag = nullptr;  // diagonals of A and B (Jacobi)
+  feast_nh_net *net = nullptr;              // learned preconditioner (not owned)
+  int net_N = 0, net_nfeat = 0;
+  float net_kappa = 1.f;
+  float *net_feat = nullptr, *net_scratch = nullptr;
+  int krylov_its = 0;         // FGMRES iterations in the current call
+  std::string fg_err;
   bool own_stream = false;
   EvPool ev_solve, ev_resid;
 };
@@ -198,9 +207,43 @@ const void *tma_ptr(const feast_nh_ctx *ctx) { return ctx->tma.empty() ? nullptr
 bool cs_mode(const feast_nh_ctx *ctx) { return ctx->o.problem == FEAST_NH_PROBLEM_COMPLEX_SYMMETRIC; }
 bool fp32(const feast_nh_ctx *ctx) { return ctx->o.precision == FEAST_NH_PREC_FP32_IR; }
 bool krylov(const feast_nh_ctx *ctx) { return ctx->o.inner_kind == FEAST_NH_INNER_BICGSTAB; }
+bool fgmres(const feast_nh_ctx *ctx) { return ctx->o.inner_kind == FEAST_NH_INNER_FGMRES; }
+bool banded(const feast_nh_ctx *ctx) { return ctx->o.inner_kind == FEAST_NH_INNER_BANDED; }
+
+// FGMRES operator and right preconditioner of one side (0: eq. qr, 1: eq. ql)
+struct FgSide {
+  feast_nh_ctx *ctx;
+  int side, m;
+};
+void fg_apply(void *p, const cxf *x, cxf *y, cudaStream_t s) {
+  const FgSide *f = static_cast<const FgSide *>(p);
+  feast_nh_ctx *ctx = f->ctx;
+  if (f->side == 0)
+    launch_multishift_spmm_f32(ctx->A, ctx->hasB ? &ctx->B : nullptr, ctx->ne, ctx->dz, 0, x, y, f->m, 0,
+                               ctx->max_nnz[0], s);
+  else
+    launch_multishift_spmm_f32(ctx->AH, ctx->hasB ? &ctx->BH : nullptr, ctx->ne, ctx->dz, 1, x, y, f->m, 0,
+                               ctx->max_nnz[1], s);
+}
+void fg_precond(void *p, const cxf *v, cxf *z, cudaStream_t s) {
+  const FgSide *f = static_cast<const FgSide *>(p);
+  feast_nh_ctx *ctx = f->ctx;
+  const size_t count = (size_t)ctx->ne * ctx->n * f->m;
+  if (ctx->o.precond == FEAST_NH_PRECOND_JACOBI) {
+    launch_fg_jacobi(v, ctx->dz, f->side, ctx->adiag, ctx->hasB ? ctx->bdiag : nullptr, z, ctx->ne, ctx->n, f->m, s);
+  } else if (ctx->o.precond == FEAST_NH_PRECOND_LEARNED && ctx->net) {
+    const size_t S = (size_t)ctx->ne * f->m;
+    const size_t np = net_precondition_scratch_floats(ctx->n, ctx->ne, f->m) - S;
+    if (net_precondition(ctx->net, v, z, ctx->ne, ctx->n, f->m, ctx->dz, f->side, ctx->net_kappa, ctx->net_feat,
+                         ctx->net_nfeat, ctx->net_scratch, ctx->net_scratch + np, s) != 0)
+      ctx->fg_err = "the learned preconditioner failed";
+  } else {
+    cudaMemcpyAsync(z, v, count * sizeof(cxf), cudaMemcpyDeviceToDevice, s);
+  }
+}
 
 void factorize(feast_nh_ctx *ctx) {
-  if (krylov(ctx)) {
+  if (!banded(ctx)) {
     ctx->factored = true;
     ctx->t_factor = 0;
     return;
@@ -280,6 +323,67 @@ void do_filter(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, cxd *Q, cxd *Qh, 
     ctx->inner_steps = it_r > it_l ? it_r : it_l;
     ctx->inner_res = rel_r > rel_l ? rel_r : rel_l;
     ctx->krylov_ok = !(ctx->inner_res > inner_tol);
+  } else if (fgmres(ctx)) {
+    // FP32 FGMRES (right preconditioner opts.precond) inside FP64 iterative
+    // refinement: each step asks FGMRES for a relative reduction of
+    // max(1e-5, the step's target); the FP64 residual decides convergence
+    const double tfg = std::fmax(1e-5, inner_tol);
+    const int restart = ctx->o.krylov_restart;
+    auto fg = [&](int side, const cxf *b, cxd *X, int mode) {
+      FgSide fs{ctx, side, m};
+      FgmresOp op{&fs, fg_apply, fg_precond};
+      double rel = 0;
+      const int k = ev_begin(ctx, ctx->ev_solve);
+      ctx->krylov_its += fgmres_solve(op, b, ctx->dfg, n, m, ne, ctx->m0, restart, ctx->o.krylov_max, tfg,
+                                      ctx->fgwork, &rel, ctx->s);
+      ev_end(ctx, ctx->ev_solve, k);
+      if (!ctx->fg_err.empty()) {
+        ctx->err = ctx->fg_err;
+        ctx->fg_err.clear();
+        throw Fail{FEAST_NH_EINVAL};
+      }
+      launch_cxf_accumulate(X, ctx->dfg, (size_t)ne * n * m, mode, ctx->s);
+    };
+    CKC(cudaMemsetAsync(ctx->d_done, 0, sizeof(int), ctx->s));
+    launch_broadcast_cxf(BY, (cxf *)ctx->Rn, (size_t)n * m, ne, ctx->s);
+    fg(0, (const cxf *)ctx->Rn, ctx->Xn, 0);
+    if (!cs) {
+      launch_broadcast_cxf(BhYh, (cxf *)ctx->Rhn, (size_t)n * m, ne, ctx->s);
+      fg(1, (const cxf *)ctx->Rhn, ctx->Xhn, 0);
+    }
+    int g = launch_colnorm2(BY, m, m, n, ctx->colp, ctx->s);
+    launch_reduce_parts(ctx->colp, g, m, ctx->bynorm2, ctx->s);
+    if (!cs) {
+      g = launch_colnorm2(BhYh, m, m, n, ctx->colp, ctx->s);
+      launch_reduce_parts(ctx->colp, g, m, ctx->bynorm2 + m, ctx->s);
+    }
+    const int steps = ctx->o.inner_max < 1 ? 1 : ctx->o.inner_max;
+    for (int it = 0; it < steps; ++it) {
+      int kr = ev_begin(ctx, ctx->ev_resid);
+      const int gm = launch_multishift_residual<float>(ctx->A, Bp, ne, ctx->dz, ctx->dw, ctx->Xn, BY, (cxf *)ctx->Rn,
+                                                       nullptr, ctx->part, m, nullptr, ctx->s);
+      ev_end(ctx, ctx->ev_resid, kr);
+      if (!cs) {
+        kr = ev_begin(ctx, ctx->ev_resid);
+        launch_multishift_residual<float>(ctx->AH, BHp, ne, ctx->dzc, ctx->dwc, ctx->Xhn, BhYh, (cxf *)ctx->Rhn,
+                                          nullptr, ctx->part + (size_t)gm * ne * m, m, nullptr, ctx->s);
+        ev_end(ctx, ctx->ev_resid, kr);
+      }
+      launch_residual_check(ctx->part, gm, ne, m, ctx->bynorm2, cs ? 1 : 2, inner_tol, ctx->d_maxrel, ctx->d_done,
+                            ctx->s);
+      CKC(cudaMemcpyAsync(ctx->h_small + 2, ctx->d_done, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+      CKC(cudaStreamSynchronize(ctx->s));
+      int done = 0;
+      std::memcpy(&done, ctx->h_small + 2, sizeof(int));
+      ctx->inner_steps = it + 1;
+      if (done) break;
+      if (it + 1 < steps) {
+        fg(0, (const cxf *)ctx->Rn, ctx->Xn, 1);
+        if (!cs) fg(1, (const cxf *)ctx->Rhn, ctx->Xhn, 1);
+      }
+    }
+    launch_node_sum(ne, ctx->dw, ctx->Xn, xns, n, m, Q, ctx->s);
+    if (!cs) launch_node_sum(ne, ctx->dwc, ctx->Xhn, xns, n, m, Qh, ctx->s);
   } else {
     // banded direct solves with iterative refinement: FP32 factors (chosen
     // form) or FP64 factors (plain form; the unpivoted factors of a general
@@ -520,6 +624,8 @@ void feast_nh_default_opts(feast_nh_opts *o) {
   o->precision = FEAST_NH_PREC_FP64;
   o->problem = FEAST_NH_PROBLEM_GENERAL;
   o->krylov_max = 1000;
+  o->krylov_restart = 30;
+  o->precond = FEAST_NH_PRECOND_JACOBI;
 }
 
 const char *feast_nh_strerror(feast_nh_status s) {
@@ -591,8 +697,15 @@ void init_ctx(feast_nh_ctx *ctx, const feast_nh_csr *A, const feast_nh_csr *B, c
     REQ(contour->kind != 2 || (contour->z && contour->w), "custom contour needs z and w");
     REQ(m0 >= 1 && m0 <= kMaxM0 && m0 <= A->n, "m0 must be in [1, min(128, n)]");
     if (opts) ctx->o = *opts; else feast_nh_default_opts(&ctx->o);
-    REQ(ctx->o.inner_kind == FEAST_NH_INNER_BANDED || ctx->o.inner_kind == FEAST_NH_INNER_BICGSTAB,
-        "inner_kind must be BANDED or BICGSTAB");
+    REQ(ctx->o.inner_kind == FEAST_NH_INNER_BANDED || ctx->o.inner_kind == FEAST_NH_INNER_BICGSTAB ||
+            ctx->o.inner_kind == FEAST_NH_INNER_FGMRES,
+        "inner_kind must be BANDED, BICGSTAB or FGMRES");
+    REQ(ctx->o.inner_kind != FEAST_NH_INNER_FGMRES || ctx->o.precision == FEAST_NH_PREC_FP32_IR,
+        "the FGMRES inner solver runs FP32 sweeps inside FP64 refinement (precision FP32_IR)");
+    REQ(ctx->o.inner_kind != FEAST_NH_INNER_FGMRES ||
+            (ctx->o.krylov_restart >= 1 && ctx->o.krylov_restart <= 64 && ctx->o.krylov_max >= 1),
+        "FGMRES needs 1 <= krylov_restart <= 64 and krylov_max >= 1");
+    REQ(ctx->o.precond >= FEAST_NH_PRECOND_NONE && ctx->o.precond <= FEAST_NH_PRECOND_LEARNED, "bad precond");
     REQ(ctx->o.inner_kind != FEAST_NH_INNER_BICGSTAB || ctx->o.precision == FEAST_NH_PREC_FP64,
         "the BiCGStab inner solver runs in FP64");
     REQ(ctx->o.inner_max >= 1, "inner_max must be >= 1");
@@ -693,7 +806,7 @@ void init_ctx(feast_nh_ctx *ctx, const feast_nh_csr *A, const feast_nh_csr *B, c
       CKC(cudaMemcpyAsync(ctx->dzf, zf.data(), ctx->nf * sizeof(cxd), cudaMemcpyHostToDevice, ctx->s));
     }
     const bool f32 = fp32(ctx);
-    const bool fits = rr_only || krylov(ctx) || (f32 ? (band_fits<float>(ctx->klp, ctx->kup) &&
+    const bool fits = rr_only || !banded(ctx) || (f32 ? (band_fits<float>(ctx->klp, ctx->kup) &&
                              (band_tma_fits(ctx->klp, ctx->kup) || band_solve_fits<float>(ctx->klp, ctx->kup)))
                           : (band_fits<double>(ctx->klp, ctx->kup) && band_solve_fits<double>(ctx->klp, ctx->kup)));
     if (!fits) {
@@ -703,21 +816,33 @@ void init_ctx(feast_nh_ctx *ctx, const feast_nh_csr *A, const feast_nh_csr *B, c
     }
     const size_t es = f32 ? sizeof(cxf) : sizeof(cxd);
     const bool inner = !rr_only;
-    const size_t band_elems = (krylov(ctx) || !inner) ? 0 : (size_t)ctx->nf * n * (ctx->klp + ctx->kup + 1);
+    const size_t band_elems = (!banded(ctx) || !inner) ? 0 : (size_t)ctx->nf * n * (ctx->klp + ctx->kup + 1);
     ctx->band = dalloc<void>(ctx, band_elems * es);
     if (krylov(ctx) && inner) ctx->kwork = dalloc<void>(ctx, krylov_work_bytes(n, m0, ne));
-    if (inner && f32 && !krylov(ctx) && band_tma_fits(ctx->klp, ctx->kup)) {
+    if (inner && f32 && banded(ctx) && band_tma_fits(ctx->klp, ctx->kup)) {
       ctx->bandT = dalloc<void>(ctx, band_elems * es);
       ctx->tma.assign(band_tma_bytes(), 0);
       if (!band_tma_make(ctx->tma.data(), n, ctx->klp, ctx->kup, ctx->nf, (const cxf *)ctx->band,
                          (const cxf *)ctx->bandT))
         ctx->tma.clear();
     }
-    const size_t yse = (krylov(ctx) || !inner) ? 0
+    const size_t yse = (!banded(ctx) || !inner) ? 0
                        : f32   ? band_solve_scratch_elems<float>(n, m0, ne)
                                : band_solve_scratch_elems<double>(n, m0, ne);
     ctx->ysc = dalloc<void>(ctx, yse * es);
-    if (inner && f32 && !krylov(ctx)) ctx->dinv = dalloc<void>(ctx, band_diag_inv_elems(n, ctx->nf) * sizeof(cxf));
+    if (inner && f32 && banded(ctx)) ctx->dinv = dalloc<void>(ctx, band_diag_inv_elems(n, ctx->nf) * sizeof(cxf));
+    if (inner && fgmres(ctx)) {
+      ctx->fgwork = dalloc<void>(ctx, fgmres_work_bytes(n, m0, ne, ctx->o.krylov_restart));
+      ctx->dfg = dalloc<cxf>(ctx, (size_t)ne * n * m0 * sizeof(cxf));
+      ctx->adiag = dalloc<cxd>(ctx, (size_t)n * sizeof(cxd));
+      launch_csr_diag(ctx->A, ctx->adiag, ctx->s);
+      if (B) {
+        ctx->bdiag = dalloc<cxd>(ctx, (size_t)n * sizeof(cxd));
+        launch_csr_diag(ctx->B, ctx->bdiag, ctx->s);
+      }
+      ctx->net_feat = dalloc<float>(ctx, 32 * sizeof(float));
+      ctx->net_scratch = dalloc<float>(ctx, net_precondition_scratch_floats(n, ne, m0) * sizeof(float));
+    }
     const size_t blk = (size_t)n * m0 * sizeof(cxd);
     if (inner) {
       ctx->Yw = dalloc<cxd>(ctx, blk);
@@ -818,6 +943,7 @@ feast_nh_status feast_nh_filter(feast_nh_ctx *ctx, const void *Y, const void *Yh
     REQ(Y && Q && Qh && m >= 1 && m <= ctx->m0, "filter: bad block pointers or m");
     REQ(cs_mode(ctx) || Yh, "filter: Yh is required unless the problem is complex symmetric");
     CKC(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->s));
+    ctx->krylov_its = 0;
     do_filter(ctx, (const cxd *)Y, (const cxd *)Yh, (cxd *)Q, (cxd *)Qh, m);
     // the filter's status: device error word and the largest relative
     // residual of the shifted solves (one small read)
@@ -867,7 +993,7 @@ feast_nh_status feast_nh_rr(feast_nh_ctx *ctx, const void *Q, const void *Qh, in
       info->max_res = ctx->h_st->max_res;
       info->kl = ctx->kl;
       info->ku = ctx->ku;
-      info->n_factorizations = krylov(ctx) ? 0 : ctx->nf;
+      info->n_factorizations = banded(ctx) ? ctx->nf : 0;
       info->pivot_min = ctx->piv_min;
       info->pivot_max = ctx->piv_max;
     }
@@ -895,6 +1021,7 @@ feast_nh_status feast_nh_solve(feast_nh_ctx *ctx, const void *Y0, const void *Yh
     ctx->factored = false;  // each solve factorises afresh and keeps the factors for its iterations
     ctx->have_prev = 0;
     ctx->n_inner_fail = 0;
+    ctx->krylov_its = 0;
     ev_harvest(ctx->ev_solve);
     ev_harvest(ctx->ev_resid);
     ctx->ev_solve.ms = ctx->ev_resid.ms = 0;
@@ -965,10 +1092,11 @@ feast_nh_status feast_nh_solve(feast_nh_ctx *ctx, const void *Y0, const void *Yh
       info->t_resid_kernel_ms = ctx->ev_resid.ms;
       info->n_solve_launches = ctx->ev_solve.launches;
       info->n_resid_launches = ctx->ev_resid.launches;
-      info->n_factorizations = krylov(ctx) ? 0 : ctx->nf;
+      info->n_factorizations = banded(ctx) ? ctx->nf : 0;
       info->inner_fail = ctx->n_inner_fail;
       info->pivot_min = ctx->piv_min;
       info->pivot_max = ctx->piv_max;
+      info->krylov_iterations = ctx->krylov_its;
     }
     if (!conv) {
       if (ctx->n_inner_fail > 0) {
@@ -1023,6 +1151,79 @@ feast_nh_status feast_nh_small_eig(feast_nh_ctx *ctx, const void *M, int32_t m, 
     std::memcpy(&herr, ctx->h_small + 1, sizeof(int));
     const feast_nh_status es = status_from_err(ctx, herr);
     if (es != FEAST_NH_OK) return es;
+  } catch (const Fail &f) {
+    return f.st;
+  }
+  return FEAST_NH_OK;
+}
+
+feast_nh_status feast_nh_set_network(feast_nh_ctx *ctx, feast_nh_net *net, int32_t N, float kappa,
+                                     const float *features, int32_t nfeat) {
+  if (!ctx) return FEAST_NH_EINVAL;
+  try {
+    REQ(fgmres(ctx), "set_network: the context's inner solver is not FGMRES");
+    REQ(net && N >= 2 && (long long)N * N == ctx->n, "set_network: the operator is not on an N x N grid (n = N^2)");
+    REQ(nfeat >= 0 && nfeat <= 28 && (nfeat == 0 || features), "set_network: 0 <= nfeat <= 28");
+    ctx->net = net;
+    ctx->net_N = N;
+    ctx->net_kappa = kappa;
+    ctx->net_nfeat = nfeat;
+    if (nfeat) CKC(cudaMemcpy(ctx->net_feat, features, nfeat * sizeof(float), cudaMemcpyHostToDevice));
+  } catch (const Fail &f) {
+    return f.st;
+  }
+  return FEAST_NH_OK;
+}
+
+feast_nh_status feast_nh_learned_pairs(feast_nh_ctx *ctx, const void *R, int32_t m, int32_t N, float kappa,
+                                      const float *features, int32_t nfeat, float *Xin, float *T) {
+  if (!ctx) return FEAST_NH_EINVAL;
+  try {
+    REQ(banded(ctx) && !ctx->rr_only, "learned_pairs: needs the banded direct solver (exact solves)");
+    REQ(R && Xin && T && m >= 1 && m <= ctx->m0, "learned_pairs: bad arguments");
+    REQ(N >= 2 && (long long)N * N == ctx->n, "learned_pairs: the operator is not on an N x N grid");
+    REQ(nfeat >= 0 && nfeat <= 28 && (nfeat == 0 || features), "learned_pairs: 0 <= nfeat <= 28");
+    CKC(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->s));
+    // exact node solutions X_j = (z_j B - A)^{-1} R (both sides are solved;
+    // the right side's node blocks are kept), refined to opts.inner_tol
+    do_filter(ctx, (const cxd *)R, (const cxd *)R, ctx->T1, ctx->T2, m);
+    float *feat = nullptr;
+    if (nfeat) {
+      feat = reinterpret_cast<float *>(ctx->cn);  // 4 * 128 doubles of room
+      CKC(cudaMemcpyAsync(feat, features, nfeat * sizeof(float), cudaMemcpyHostToDevice, ctx->s));
+    }
+    const int g = launch_colnorm2((const cxd *)R, m, m, ctx->n, ctx->colp, ctx->s);
+    launch_reduce_parts(ctx->colp, g, m, ctx->bynorm2, ctx->s);
+    launch_learned_pairs((const cxd *)R, ctx->Xn, ctx->ne, ctx->n, m, ctx->dz, kappa, feat, nfeat, ctx->bynorm2, Xin,
+                         T, ctx->s);
+    check_launch(ctx, "learned_pairs");
+    CKC(cudaMemcpyAsync(ctx->h_small, ctx->d_maxrel, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+    CKC(cudaStreamSynchronize(ctx->s));
+    if (!(ctx->h_small[0] <= ctx->o.inner_tol)) {
+      ctx->err = "learned_pairs: the shifted solves stopped above inner_tol";
+      return FEAST_NH_EINNER;
+    }
+  } catch (const Fail &f) {
+    return f.st;
+  }
+  return FEAST_NH_OK;
+}
+
+feast_nh_status feast_nh_operator_loss(feast_nh_ctx *ctx, const float *out, const float *T, int32_t m, int32_t N,
+                                      int32_t side, float *gout, double *loss) {
+  if (!ctx) return FEAST_NH_EINVAL;
+  try {
+    REQ(out && T && gout && loss && m >= 1 && m <= ctx->m0 && (side == 0 || side == 1), "operator_loss: bad arguments");
+    REQ(N >= 2 && (long long)N * N == ctx->n, "operator_loss: the operator is not on an N x N grid");
+    double *dl = ctx->d_maxrel;  // one double of device scratch
+    CKC(cudaMemsetAsync(dl, 0, sizeof(double), ctx->s));
+    const CsrView &M = side == 0 ? ctx->A : ctx->AH;
+    const CsrView &MH = side == 0 ? ctx->AH : ctx->A;
+    float *ybuf = reinterpret_cast<float *>(ctx->dfg ? (void *)ctx->dfg : (void *)ctx->Xn);
+    launch_operator_loss(M, MH, ctx->ne, ctx->n, m, ctx->dz, side, out, T, ybuf, gout, dl, ctx->s);
+    check_launch(ctx, "operator_loss");
+    CKC(cudaMemcpyAsync(loss, dl, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+    CKC(cudaStreamSynchronize(ctx->s));
   } catch (const Fail &f) {
     return f.st;
   }

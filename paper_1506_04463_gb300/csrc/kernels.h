@@ -147,6 +147,44 @@ void launch_csr_diag(const CsrView &A, cxd *diag, cudaStream_t s);
 // Deterministic fill of a block with values in [-1, 1] (autotuning input).
 void launch_fill_pattern(cxd *X, size_t count, cudaStream_t s);
 
+// ---------------- fgmres.cu : batched flexible GMRES (FP32) -----------------
+// The operator (y = (z_j B - A) x for every node, node-major complex-float
+// blocks) and the right preconditioner (z ~ (z_j B - A)^{-1} v), supplied by
+// the caller.
+struct FgmresOp {
+  void *ctx;
+  void (*apply)(void *ctx, const cxf *x, cxf *y, cudaStream_t s);
+  void (*precond)(void *ctx, const cxf *v, cxf *z, cudaStream_t s);
+};
+size_t fgmres_work_bytes(int n, int m0, int ne, int kmax);
+// Solves op(d) = b for every (node, column) system to |b - op d| <= tol |b|
+// (or maxit iterations) with restart length kmax; d (node-major, complex
+// float) is overwritten.  Returns the iterations done; *maxrel gets the
+// largest true relative residual.
+int fgmres_solve(const FgmresOp &op, const cxf *b, cxf *d, int n, int m, int ne, int m0, int kmax, int maxit,
+                 double tol, void *work, double *maxrel, cudaStream_t s);
+void launch_fg_jacobi(const cxf *v, const cxd *zn, int conj_z, const cxd *adiag, const cxd *bdiag, cxf *z, int ne,
+                      int n, int m, cudaStream_t s);
+
+void launch_cxf_accumulate(cxd *X, const cxf *d, size_t count, int mode, cudaStream_t s);
+void launch_broadcast_cxf(const cxd *BY, cxf *out, size_t nm, int ne, cudaStream_t s);
+
+// ---------------- net.cu : the learned preconditioner's network ----------------
+struct feast_nh_net;
+// z = network(v) for all ne*m systems of a node-major complex-float block on
+// the net's N x N grid (n = N^2); part/rms: scratch of
+// net_precondition_scratch_floats floats.
+int net_precondition(feast_nh_net *net, const cxf *v, cxf *z, int ne, int n, int m, const cxd *zn, int conj_z,
+                     float kappa, const float *feat, int nfeat, float *part, float *rms, cudaStream_t s);
+size_t net_precondition_scratch_floats(int n, int ne, int m);
+int *net_error_word(feast_nh_net *n);
+// Training pairs for the network from node solutions X (node-major) of R.
+void launch_learned_pairs(const cxd *R, const cxd *X, int ne, int n, int m, const cxd *z, float kappa,
+                          const float *feat, int nfeat, const double *rn2, float *Xin, float *T, cudaStream_t s);
+// Operator-norm loss || (z_j I - A)(out - T) ||^2 of network output images and its gradient.
+void launch_operator_loss(const CsrView &M, const CsrView &MH, int ne, int n, int m, const cxd *z, int side,
+                          const float *out, const float *T, float *ybuf, float *gout, double *loss, cudaStream_t s);
+
 // ---------------- dense.cu : tall-skinny and small dense kernels -----------
 // G = X^H Y (mx x my), X: n x mx (ld ldx), Y: n x my (ld ldy); partial buffer
 // of size nchunks*mx*my complex.

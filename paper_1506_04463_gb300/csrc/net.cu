@@ -22,6 +22,7 @@
 // The backward data pass is the same kernel with the weights flipped and
 // their channel axes swapped; the weight gradient is a CUDA-core reduction
 // over pixels (per-CTA partials, fixed-order sum).
+#include <algorithm>
 #include <cuda_bf16.h>
 #include "kernels.h"
 
@@ -339,6 +340,168 @@ __global__ void k_bf16_to_f32(const __nv_bfloat16 *x, float *y, long long count)
     y[e] = __bfloat162float(x[e]);
 }
 
+// Per-system RMS of a node-major block (system s = j*m + c over its n rows):
+// per-CTA partial sums of |v|^2, then a fixed-order reduction.
+__global__ void k_sys_norm2(const cxf *v, int ne, int n, int m, int rows_per_cta, float *part) {
+  const int S = ne * m;
+  const int r0 = blockIdx.x * rows_per_cta, r1 = min(n, r0 + rows_per_cta);
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    const int j = s / m, c = s - j * m;
+    float acc = 0.f;
+    for (int i = r0; i < r1; ++i) acc += abs2(v[((size_t)j * n + i) * m + c]);
+    part[(size_t)blockIdx.x * S + s] = acc;
+  }
+}
+__global__ void k_sys_rms(const float *part, int nparts, int S, int n, float *rms) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  double a = 0.0;
+  for (int p = 0; p < nparts; ++p) a += part[(size_t)p * S + s];
+  const double r = sqrt(a / n);
+  rms[s] = r > 0 ? (float)r : 1.f;
+}
+// Image of system s0 + q (q < cnt), pixel i = y N + x: channels
+// [Re v / rms, Im v / rms, kappa Re z_j, kappa Im z_j, features..., 0...].
+__global__ void k_net_pack(const cxf *v, int ne, int n, int m, int s0, int cnt, const cxd *z, int conj_z, float kappa,
+                           const float *feat, int nfeat, const float *rms, __nv_bfloat16 *act) {
+  const long long total = (long long)cnt * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(e % cnt), i = (int)(e / cnt);  // systems fastest: coalesced reads of v
+    const int s = s0 + q, j = s / m, c = s - j * m;
+    const cxf val = v[((size_t)j * n + i) * m + c];
+    const float inv = 1.f / rms[s];
+    cxd zz = z[j];
+    if (conj_z) zz = conj(zz);
+    float ch[kC];
+#pragma unroll
+    for (int k = 0; k < kC; ++k) ch[k] = 0.f;
+    ch[0] = val.re * inv;
+    ch[1] = val.im * inv;
+    ch[2] = kappa * (float)zz.re;
+    ch[3] = kappa * (float)zz.im;
+    for (int k = 0; k < nfeat && k < kC - 4; ++k) ch[4 + k] = feat[k];
+    uint4 *dst = reinterpret_cast<uint4 *>(act + ((size_t)q * n + i) * kC);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      __nv_bfloat162 h[4];
+#pragma unroll
+      for (int w = 0; w < 4; ++w) h[w] = __floats2bfloat162_rn(ch[u * 8 + 2 * w], ch[u * 8 + 2 * w + 1]);
+      dst[u] = *reinterpret_cast<uint4 *>(h);
+    }
+  }
+}
+// z (system s0 + q) = rms * (out0 + i out1)
+__global__ void k_net_unpack(const float *outf, int ne, int n, int m, int s0, int cnt, const float *rms, cxf *z) {
+  const long long total = (long long)cnt * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(e % cnt), i = (int)(e / cnt);
+    const int s = s0 + q, j = s / m, c = s - j * m;
+    const float2 o = *reinterpret_cast<const float2 *>(outf + ((size_t)q * n + i) * kC);
+    z[((size_t)j * n + i) * m + c] = mk(rms[s] * o.x, rms[s] * o.y);
+  }
+}
+
+// Training pairs from exact solves.  Inputs: the image of system s = (j, c)
+// is column c of R (shared by the nodes) packed as the preconditioner packs
+// its input (Re, Im over the column's RMS, kappa z_j, features), FP32.
+// Targets: X_j[:, c] over its own RMS (the direction of the correction).
+__global__ void k_pairs_inputs(const cxd *R, int ne, int n, int m, const cxd *z, float kappa, const float *feat,
+                               int nfeat, const double *rn2, float *Xin) {
+  const long long total = (long long)ne * m * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(e / n), i = (int)(e - (long long)s * n);
+    const int j = s / m, c = s - j * m;
+    const double rms = sqrt(rn2[c] / n);
+    const double inv = rms > 0 ? 1.0 / rms : 1.0;
+    const cxd v = R[(size_t)i * m + c];
+    float *o = Xin + ((size_t)s * n + i) * kC;
+    o[0] = (float)(v.re * inv);
+    o[1] = (float)(v.im * inv);
+    o[2] = kappa * (float)z[j].re;
+    o[3] = kappa * (float)z[j].im;
+    for (int k = 4; k < kC; ++k) o[k] = (k - 4 < nfeat) ? feat[k - 4] : 0.f;
+  }
+}
+// targets: the node solution for the normalised column, X_j[:, c] / rms(R[:, c])
+__global__ void k_pairs_targets(const cxd *X, int ne, int n, int m, const double *rn2, float *T) {
+  const long long total = (long long)ne * m * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(e / n), i = (int)(e - (long long)s * n);
+    const int j = s / m, c = s - j * m;
+    const double rms = sqrt(rn2[c] / n);
+    const double inv = rms > 0 ? 1.0 / rms : 1.0;
+    const cxd v = X[((size_t)j * n + i) * m + c];
+    T[((size_t)s * n + i) * 2] = (float)(v.re * inv);
+    T[((size_t)s * n + i) * 2 + 1] = (float)(v.im * inv);
+  }
+}
+void launch_learned_pairs(const cxd *R, const cxd *X, int ne, int n, int m, const cxd *z, float kappa,
+                          const float *feat, int nfeat, const double *rn2, float *Xin, float *T, cudaStream_t s) {
+  k_pairs_inputs<<<grid_for((size_t)ne * m * n), 256, 0, s>>>(R, ne, n, m, z, kappa, feat, nfeat, rn2, Xin);
+  note_launch();
+  k_pairs_targets<<<grid_for((size_t)ne * m * n), 256, 0, s>>>(X, ne, n, m, rn2, T);
+  note_launch();
+}
+
+// Operator-norm loss of the network output against exact corrections: for
+// system s = (j, c), d = out_s - T_s (channels 0, 1 as a complex image),
+// y = (z_j I - A) d (the node's shifted operator applied on the grid; conj(z_j)
+// and A^H for side 1), loss = sum |y|^2 / count, and its gradient with
+// respect to out, g = 2 (z_j I - A)^H y / count, written to channels 0, 1 of
+// gout (32 channels, others zero).  With T the exact correction of the input
+// residual, y = (z_j I - A) out_s - r_s.
+__global__ void k_oploss_apply(CsrView M, int ne, int n, int m, const cxd *z, int conj_z, const float *out,
+                               const float *T, float *y, double *loss) {
+  const long long total = (long long)ne * m * n;
+  double local = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(e / n), i = (int)(e - (long long)s * n);
+    const int j = s / m;
+    cxd zj = z[j];
+    if (conj_z) zj = conj(zj);
+    auto dval = [&](int k) {
+      const float *o = out + ((size_t)s * n + k) * 32;
+      const float *t = T + ((size_t)s * n + k) * 2;
+      return mk((double)o[0] - t[0], (double)o[1] - t[1]);
+    };
+    cxd acc = zj * dval(i);
+    for (int64_t k = M.rowptr[i]; k < M.rowptr[i + 1]; ++k) cfms(acc, csr_val(M, k), dval(M.colind[k]));
+    y[((size_t)s * n + i) * 2] = (float)acc.re;
+    y[((size_t)s * n + i) * 2 + 1] = (float)acc.im;
+    local += abs2(acc);
+  }
+  for (int o = 16; o; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, local / (double)total);
+}
+__global__ void k_oploss_grad(CsrView MH, int ne, int n, int m, const cxd *z, int conj_z, const float *y,
+                              float *gout) {
+  const long long total = (long long)ne * m * n;
+  const double sc = 2.0 / (double)total;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(e / n), i = (int)(e - (long long)s * n);
+    const int j = s / m;
+    cxd zj = z[j];
+    if (!conj_z) zj = conj(zj);  // adjoint of (z I - A) is (conj z I - A^H)
+    auto yv = [&](int k) {
+      const float *q = y + ((size_t)s * n + k) * 2;
+      return mk((double)q[0], (double)q[1]);
+    };
+    cxd acc = zj * yv(i);
+    for (int64_t k = MH.rowptr[i]; k < MH.rowptr[i + 1]; ++k) cfms(acc, csr_val(MH, k), yv(MH.colind[k]));
+    float *g = gout + ((size_t)s * n + i) * 32;
+    g[0] = (float)(sc * acc.re);
+    g[1] = (float)(sc * acc.im);
+    for (int k = 2; k < 32; ++k) g[k] = 0.f;
+  }
+}
+void launch_operator_loss(const CsrView &M, const CsrView &MH, int ne, int n, int m, const cxd *z, int side,
+                          const float *out, const float *T, float *ybuf, float *gout, double *loss, cudaStream_t s) {
+  k_oploss_apply<<<grid_for((size_t)ne * m * n), 256, 0, s>>>(M, ne, n, m, z, side, out, T, ybuf, loss);
+  note_launch();
+  k_oploss_grad<<<grid_for((size_t)ne * m * n), 256, 0, s>>>(MH, ne, n, m, z, side, ybuf, gout);
+  note_launch();
+}
+
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
@@ -414,6 +577,7 @@ void launch_bf16_to_f32(const void *x, float *y, long long count, cudaStream_t s
 // ---------------------------------------------------------------------------
 // network object (C ABI in feast_nh.h)
 // ---------------------------------------------------------------------------
+#include <algorithm>
 #include <string>
 #include <vector>
 #include "feast_nh.h"
@@ -495,6 +659,37 @@ feast_nh_status net_apply_internal(feast_nh_net *n, int nimg, const float **out)
   return st;
 }
 void *net_input_buffer(feast_nh_net *n) { return n->act[0]; }
+
+// z = network(v) for every system of a node-major block (images of the
+// N x N grid, n = N^2), in chunks of at most max_images systems.
+int net_precondition(feast_nh_net *net, const cxf *v, cxf *z, int ne, int n, int m, const cxd *zn,
+                                 int conj_z, float kappa, const float *feat, int nfeat, float *part, float *rms,
+                                 cudaStream_t s) {
+  if ((long long)net->N * net->N != n) return FEAST_NH_EINVAL;
+  const int S = ne * m;
+  const int parts = std::min(1216, n);
+  const int rpc = ceil_div(n, parts), np = ceil_div(n, rpc);
+  k_sys_norm2<<<np, 256, 0, s>>>(v, ne, n, m, rpc, part);
+  note_launch();
+  k_sys_rms<<<ceil_div(S, 256), 256, 0, s>>>(part, np, S, n, rms);
+  note_launch();
+  for (int s0 = 0; s0 < S; s0 += net->maxi) {
+    const int cnt = std::min(net->maxi, S - s0);
+    k_net_pack<<<grid_for((size_t)cnt * n), 256, 0, s>>>(v, ne, n, m, s0, cnt, zn, conj_z, kappa, feat, nfeat, rms,
+                                                         net->act[0]);
+    note_launch();
+    cudaStream_t keep = net->s;
+    net->s = s;
+    const feast_nh_status st = net_forward(net, cnt);
+    net->s = keep;
+    if (st != FEAST_NH_OK) return st;
+    k_net_unpack<<<grid_for((size_t)cnt * n), 256, 0, s>>>(net->outf, ne, n, m, s0, cnt, rms, z);
+    note_launch();
+  }
+  return FEAST_NH_OK;
+}
+size_t net_precondition_scratch_floats(int n, int ne, int m) { return (size_t)std::min(1216, n) * ne * m + ne * m; }
+int *net_error_word(feast_nh_net *n) { return n->derr; }
 int net_grid(const feast_nh_net *n) { return n->N; }
 int net_max_images(const feast_nh_net *n) { return n->maxi; }
 
@@ -582,22 +777,14 @@ feast_nh_status feast_nh_net_forward(feast_nh_net *n, const float *x, float *out
   return net_check(n);
 }
 
-feast_nh_status feast_nh_net_train_step(feast_nh_net *n, const float *x, const float *target, int32_t cout,
-                                        int32_t nimg, float lr, double *loss, float *grad_out) {
-  if (!n || !x || !target || cout < 1 || cout > kC || nimg < 1 || nimg > n->maxi || lr < 0) return FEAST_NH_EINVAL;
+// Backward pass from dL/d out (FP32, 32 channels) through the activations of
+// the last forward call, then an optional Adam step.
+static feast_nh_status net_backward(feast_nh_net *n, __nv_bfloat16 *g, int nimg, float lr, float *grad_out) {
   cudaStream_t s = n->s;
-  const long long npix = (long long)nimg * n->N * n->N;
-  cudaMemsetAsync(n->derr, 0, sizeof(int), s);
-  cudaMemsetAsync(n->dloss, 0, sizeof(double), s);
-  launch_to_bf16(x, n->act[0], npix * kC, s);
-  feast_nh_status st = net_forward(n, nimg);
-  if (st != FEAST_NH_OK) return st;
-  launch_net_loss_grad(n->outf, target, cout, npix, n->g0, n->dloss, s);
-  __nv_bfloat16 *g = n->g0, *gn = n->g1;
+  __nv_bfloat16 *gn = (g == n->g0) ? n->g1 : n->g0;
   for (int l = n->L - 1; l >= 0; --l) {
     launch_conv_wgrad(n->act[l], g, nimg, n->N, n->wpart, n->grad + (size_t)l * kLayerP, s);
     if (l > 0) {
-      // gradient of the layer's input, masked by relu' of the layer below
       launch_conv_adjoint_weights(n->wb + (size_t)l * kLayerW, n->wt, s);
       const cudaError_t e = launch_conv3x3_tc(g, n->wt, nullptr, n->act[l], 0, gn, nullptr, nimg, n->N, n->derr, s);
       if (e != cudaSuccess) {
@@ -617,6 +804,32 @@ feast_nh_status feast_nh_net_train_step(feast_nh_net *n, const float *x, const f
       launch_net_adam(n->params + (size_t)l * kLayerP, n->grad + (size_t)l * kLayerP, n->m1 + (size_t)l * kLayerP,
                       n->m2 + (size_t)l * kLayerP, kLayerP, lr, n->t, n->wb + (size_t)l * kLayerW, kLayerW, s);
   }
+  return FEAST_NH_OK;
+}
+
+feast_nh_status feast_nh_net_backward(feast_nh_net *n, const float *gout, int32_t nimg, float lr, float *grad) {
+  if (!n || !gout || nimg < 1 || nimg > n->maxi || lr < 0) return FEAST_NH_EINVAL;
+  const long long npix = (long long)nimg * n->N * n->N;
+  cudaMemsetAsync(n->derr, 0, sizeof(int), n->s);
+  launch_to_bf16(gout, n->g0, npix * kC, n->s);
+  const feast_nh_status st = net_backward(n, n->g0, nimg, lr, grad);
+  if (st != FEAST_NH_OK) return st;
+  return net_check(n);
+}
+
+feast_nh_status feast_nh_net_train_step(feast_nh_net *n, const float *x, const float *target, int32_t cout,
+                                        int32_t nimg, float lr, double *loss, float *grad_out) {
+  if (!n || !x || !target || cout < 1 || cout > kC || nimg < 1 || nimg > n->maxi || lr < 0) return FEAST_NH_EINVAL;
+  cudaStream_t s = n->s;
+  const long long npix = (long long)nimg * n->N * n->N;
+  cudaMemsetAsync(n->derr, 0, sizeof(int), s);
+  cudaMemsetAsync(n->dloss, 0, sizeof(double), s);
+  launch_to_bf16(x, n->act[0], npix * kC, s);
+  feast_nh_status st = net_forward(n, nimg);
+  if (st != FEAST_NH_OK) return st;
+  launch_net_loss_grad(n->outf, target, cout, npix, n->g0, n->dloss, s);
+  st = net_backward(n, n->g0, nimg, lr, grad_out);
+  if (st != FEAST_NH_OK) return st;
   if (loss && cudaMemcpyAsync(loss, n->dloss, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return FEAST_NH_ECUDA;
   return net_check(n);

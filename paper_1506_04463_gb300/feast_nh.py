@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(_HERE, "libfeast_nh.so")
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EINNER, ESINGULAR, ETIMEOUT = range(8)
 DEVERR_ZERO_PIVOT, DEVERR_QR_NOCONV, DEVERR_TIMEOUT = 1, 2, 16
 R64, C64 = 0, 1
-INNER_BANDED, INNER_BICGSTAB = 0, 1
+INNER_BANDED, INNER_BICGSTAB, INNER_FGMRES = 0, 1, 2
+PRECOND_NONE, PRECOND_JACOBI, PRECOND_LEARNED = 0, 1, 2
 PREC_FP64, PREC_FP32_IR = 0, 1
 PROBLEM_GENERAL, PROBLEM_COMPLEX_SYMMETRIC = 0, 1
 
@@ -38,7 +39,7 @@ class Opts(C.Structure):
     _fields_ = [("eps", C.c_double), ("eta", C.c_double), ("mu", C.c_double), ("inner_tol", C.c_double),
                 ("max_iter", C.c_int32), ("inner_max", C.c_int32), ("inner_kind", C.c_int32),
                 ("precision", C.c_int32), ("problem", C.c_int32), ("timing", C.c_int32),
-                ("krylov_max", C.c_int32)]
+                ("krylov_max", C.c_int32), ("krylov_restart", C.c_int32), ("precond", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -48,7 +49,8 @@ class Info(C.Structure):
                 ("t_factor_ms", C.c_double), ("t_filter_ms", C.c_double), ("t_rr_ms", C.c_double),
                 ("t_total_ms", C.c_double), ("t_solve_kernel_ms", C.c_double), ("t_resid_kernel_ms", C.c_double),
                 ("n_solve_launches", C.c_int32), ("n_resid_launches", C.c_int32), ("n_factorizations", C.c_int32),
-                ("inner_fail", C.c_int32), ("pivot_min", C.c_double), ("pivot_max", C.c_double)]
+                ("inner_fail", C.c_int32), ("pivot_min", C.c_double), ("pivot_max", C.c_double),
+                ("krylov_iterations", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -71,7 +73,8 @@ EXPORTS = ["feast_nh_default_opts", "feast_nh_init", "feast_nh_filter", "feast_n
            "feast_nh_small_eig", "feast_nh_inject_device_error", "feast_nh_batch_init", "feast_nh_batch_solve",
            "feast_nh_batch_destroy", "feast_nh_batch_last_error", "feast_nh_multishift_spmm", "feast_nh_net_create",
            "feast_nh_net_set_params", "feast_nh_net_get_params", "feast_nh_net_forward", "feast_nh_net_train_step",
-           "feast_nh_net_destroy", "feast_nh_net_last_error"]
+           "feast_nh_net_destroy", "feast_nh_net_last_error", "feast_nh_set_network", "feast_nh_learned_pairs",
+           "feast_nh_operator_loss", "feast_nh_net_backward"]
 
 _lib = None
 
@@ -128,6 +131,14 @@ def lib():
     for f in ("feast_nh_net_create", "feast_nh_net_set_params", "feast_nh_net_get_params", "feast_nh_net_forward",
               "feast_nh_net_train_step"):
         getattr(L, f).restype = i32
+    L.feast_nh_set_network.argtypes = [vp, vp, i32, C.c_float, C.POINTER(C.c_float), i32]
+    L.feast_nh_set_network.restype = i32
+    L.feast_nh_learned_pairs.argtypes = [vp, vp, i32, i32, C.c_float, C.POINTER(C.c_float), i32, vp, vp]
+    L.feast_nh_learned_pairs.restype = i32
+    L.feast_nh_operator_loss.argtypes = [vp, vp, vp, i32, i32, i32, vp, C.POINTER(C.c_double)]
+    L.feast_nh_operator_loss.restype = i32
+    L.feast_nh_net_backward.argtypes = [vp, vp, i32, C.c_float, vp]
+    L.feast_nh_net_backward.restype = i32
     L.feast_nh_kernel_launches.argtypes = []
     L.feast_nh_kernel_launches.restype = C.c_uint64
     for f in ("feast_nh_init", "feast_nh_filter", "feast_nh_rr", "feast_nh_solve", "feast_nh_nodes",
@@ -354,6 +365,40 @@ class FeastNH:
         self._check(st, "feast_nh_small_eig")
         return lam, V
 
+    def learned_pairs(self, R, N, kappa=1.0, features=()):
+        """(inputs, targets) for the network from exact solves of R (n x m):
+        (ne*m, N, N, 32) and (ne*m, N, N, 2) float32 device tensors."""
+        Rc = R.to(torch.complex128).contiguous()
+        m = Rc.shape[1]
+        S = self.ne * m
+        Xin = torch.empty((S, N, N, NET_CH), dtype=torch.float32, device=self.device)
+        T = torch.empty((S, N, N, 2), dtype=torch.float32, device=self.device)
+        f = np.ascontiguousarray(np.asarray(features, np.float32))
+        st = lib().feast_nh_learned_pairs(self.h, _ptr(Rc), m, int(N), float(kappa),
+                                          f.ctypes.data_as(C.POINTER(C.c_float)) if f.size else None, int(f.size),
+                                          _ptr(Xin), _ptr(T))
+        self._check(st, "feast_nh_learned_pairs")
+        return Xin, T
+
+    def operator_loss(self, out, T, N, side=0):
+        """Operator-norm loss of network outputs against exact corrections and
+        its gradient with respect to the outputs."""
+        out, T = out.contiguous(), T.contiguous()
+        m = out.shape[0] // self.ne
+        g = torch.empty_like(out)
+        loss = C.c_double()
+        st = lib().feast_nh_operator_loss(self.h, _ptr(out), _ptr(T), m, int(N), int(side), _ptr(g), C.byref(loss))
+        self._check(st, "feast_nh_operator_loss")
+        return loss.value, g
+
+    def set_network(self, net, N, kappa=1.0, features=()):
+        """Attach a trained Net as the FGMRES right preconditioner."""
+        f = np.ascontiguousarray(np.asarray(features, np.float32))
+        self._net = net  # the context does not own the network; keep it alive
+        st = lib().feast_nh_set_network(self.h, net.h, int(N), float(kappa),
+                                        f.ctypes.data_as(C.POINTER(C.c_float)) if f.size else None, int(f.size))
+        self._check(st, "feast_nh_set_network")
+
     def inject_device_error(self, bits):
         """Host-side fault injection: the next filter ORs `bits` into the
         device error word (no device fault is made)."""
@@ -493,6 +538,14 @@ class Net:
                                                   float(lr), C.byref(loss), _ptr(grad)), "train_step")
         return loss.value, grad
 
+    def backward(self, gout, lr, want_grad=False):
+        """Backward from d loss / d out of the last forward, optional Adam step."""
+        gout = gout.contiguous()
+        grad = torch.empty(self.layers * NET_LAYER_PARAMS, dtype=torch.float32, device=self.device) \
+            if want_grad else None
+        self._check(lib().feast_nh_net_backward(self.h, _ptr(gout), gout.shape[0], float(lr), _ptr(grad)), "backward")
+        return grad
+
     def close(self):
         if getattr(self, "h", None):
             lib().feast_nh_net_destroy(self.h)
@@ -503,3 +556,34 @@ class Net:
             self.close()
         except Exception:
             pass
+
+
+def train_operator_loss(net, ctx, Xin, T, N, steps, lr, batch, generator=None):
+    """Training loop of the learned preconditioner on exact-solve pairs (the
+    arithmetic runs in the library: forward, operator-norm loss, backward,
+    Adam).  Batches of `batch` whole node groups (all ne systems of a column
+    are kept together, as feast_nh_operator_loss pairs image s with node
+    s // m).  Returns the losses."""
+    ne = ctx.ne
+    m = Xin.shape[0] // ne
+    losses = []
+    cols = max(1, batch // ne)
+    for _ in range(steps):
+        c = torch.randperm(m, generator=generator, device="cpu")[:cols]
+        idx = (torch.arange(ne)[:, None] * m + c[None, :]).reshape(-1).to(Xin.device)
+        out = net.forward(Xin[idx])
+        loss, g = _batch_operator_loss(ctx, out, T[idx], N, ne, cols)
+        net.backward(g, lr)
+        losses.append(loss)
+    return losses
+
+
+def _batch_operator_loss(ctx, out, T, N, ne, cols):
+    # the selected images are node-major (j * cols + c): the same layout the
+    # library uses for ne nodes x cols columns
+    out, T = out.contiguous(), T.contiguous()
+    g = torch.empty_like(out)
+    loss = C.c_double()
+    st = lib().feast_nh_operator_loss(ctx.h, _ptr(out), _ptr(T), cols, int(N), 0, _ptr(g), C.byref(loss))
+    ctx._check(st, "feast_nh_operator_loss")
+    return loss.value, g
