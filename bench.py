@@ -50,6 +50,7 @@ def parse():
                         "problems of uneven size in one batched solve")
     p.add_argument("--nprob", type=int, default=64)
     p.add_argument("--nmax", type=int, default=200000)
+    p.add_argument("--max-iter", type=int, default=30, help="outer iteration cap of the batched solve")
     return p.parse_args()
 
 
@@ -602,22 +603,29 @@ def run_batched(args, rank, world, local_rank):
     nmax], 9 entries per row, diagonal + U(0, 4)), each with a circle at the
     right edge of its spectrum, m0 = 48, ne = 8: one batched solve per step."""
     from paper_1506_04463_gb300 import workloads as wl
+    def log(msg):
+        print(f"[bench batched] {msg}", file=sys.stderr, flush=True)
     t0 = time.perf_counter()
     bw = wl.config4(nprob=args.nprob, nmax=args.nmax, seed=rank, workers=host_cores())
     t_gen = time.perf_counter() - t0
+    log(f"workload: {args.nprob} problems, sum n = {sum(a.shape[0] for a in bw.A)}, {t_gen:.1f} s")
     import torch
     from paper_1506_04463_gb300 import feast_nh as F
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     prec = F.PREC_FP32_IR if args.form == "chosen" else F.PREC_FP64
     t0 = time.perf_counter()
-    b = F.FeastBatch(bw.A, bw.contours, bw.m0, device=dev, precision=prec)
+    b = F.FeastBatch(bw.A, bw.contours, bw.m0, device=dev, precision=prec, max_iter=args.max_iter)
     t_init = time.perf_counter() - t0
+    log(f"batch init (transposes, workspace, launch-shape tuner): {t_init:.1f} s")
     Y0 = torch.from_numpy(bw.Y0).to(dev)
     Yh0 = torch.from_numpy(bw.Yh0).to(dev)
     stream = torch.cuda.current_stream(dev)
     for _ in range(args.warmup):
+        t1 = time.perf_counter()
         out = b.solve(Y0, Yh0)
+        torch.cuda.synchronize()
+        log(f"warm-up solve {time.perf_counter() - t1:.1f} s: {json.dumps(out['info'])}")
     torch.cuda.synchronize()
     if world > 1:
         import torch.distributed as dist
@@ -632,7 +640,9 @@ def run_batched(args, rank, world, local_rank):
         starts[k].record(stream)
         out = b.solve(Y0, Yh0)
         ends[k].record(stream)
-        found.append(sum(pb["m"] for pb in out["problems"]))
+        # pairs at eq. (res) <= 1e-10 (a problem stopped by the iteration cap
+        # may carry pairs above it)
+        found.append(sum(int((pb["res"] <= 1e-10).sum().item()) for pb in out["problems"]))
     torch.cuda.synchronize()
     launches = F.kernel_launches() - l0
     clocks = clk.stop()
@@ -660,6 +670,7 @@ def run_batched(args, rank, world, local_rank):
                        "parallelism": f"replicas x{world}", "l2": "working set far above L2"},
             "gpu_launches": int(launches), "clocks": clocks,
             "check": {"pairs_per_solve": found[-1], "problems_converged": inf["converged_problems"],
+                      "iterations_per_problem": [pb["iterations"] for pb in out["problems"]],
                       "problems_with_m_equal_edge_count": exact_ok, "max_res": max_res,
                       "iterations": inf["iterations"], "krylov_iterations": inf["krylov_iterations"],
                       "refine_steps": inf["refine_steps"], "inner_fail": inf["inner_fail"]},

@@ -1361,13 +1361,13 @@ void batch_autotune(feast_nh_batch *b) {
   launch_fill_pattern(b->Yh, b->ntot * b->m0, b->s);
   float best = 1e30f;
   int bt = 256, bg = 0, br = 128;
-  const int threads_c[] = {128, 256, 384, 512};
-  const int rows_c[] = {32, 128, 512};
+  const int threads_c[] = {256, 512};
+  const int rows_c[] = {64, 256};
   BCK(cudaEventRecord(b->ev[2], b->s));
   for (int th : threads_c) {
     const int occ = batch_fp32(b) ? batch_filter_max_ctas_per_sm<float>(th) : batch_filter_max_ctas_per_sm<double>(th);
     if (occ < 1) continue;
-    for (int per_sm = 1; per_sm <= std::min(occ, 4); per_sm *= 2)
+    for (int per_sm = 1; per_sm <= std::min(occ, 2); per_sm *= 2)
       for (int rows : rows_c) {
         batch_tiles(b, rows);
         b->threads = th;
@@ -1496,7 +1496,7 @@ feast_nh_status feast_nh_batch_init(feast_nh_batch **out, int32_t nprob, const f
     for (int k = 0; k < 9; ++k) b->L.kblk[k] = balloc<void>(b, nblk * es);
     // tiles: room for the smallest tile size the tuner tries
     int maxt = 0;
-    for (int p = 0; p < nprob; ++p) maxt += ceil_div(b->hp[p].n, 32);
+    for (int p = 0; p < nprob; ++p) maxt += ceil_div(b->hp[p].n, 64);
     b->max_tiles = maxt;
     b->dtiles = balloc<BatchTile>(b, (size_t)maxt * sizeof(BatchTile));
     b->dprob = balloc<BatchProb>(b, (size_t)nprob * sizeof(BatchProb));

@@ -336,9 +336,21 @@ def config4(nprob: int = 64, nmin: int = 5000, nmax: int = 200000, m0: int = 48,
     args = [(p, int(n), m0) for p, n in enumerate(sizes)]
     if workers and workers > 1 and nprob > 1:
         import multiprocessing as mp
+        import os
         from concurrent.futures import ProcessPoolExecutor
-        with ProcessPoolExecutor(max_workers=min(workers, nprob), mp_context=mp.get_context("spawn")) as ex_:
-            parts = list(ex_.map(_config4_problem, args))
+        # one BLAS thread per worker process: the workers already fill the cores
+        keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+        saved = {k: os.environ.get(k) for k in keys}
+        os.environ.update({k: "1" for k in keys})
+        try:
+            with ProcessPoolExecutor(max_workers=min(workers, nprob), mp_context=mp.get_context("spawn")) as ex_:
+                parts = list(ex_.map(_config4_problem, args))
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
     else:
         parts = [_config4_problem(a) for a in args]
     A, cons, ex, Y, Yh = [], [], [], [], []
