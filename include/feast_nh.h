@@ -321,7 +321,9 @@ feast_nh_status feast_nh_multishift_residual_noalloc(const feast_nh_csr *A, cons
  * Rayleigh-Ritz step of each problem (Fig. alg:three steps 2-5) then runs
  * on that problem's own stream, all problems concurrently.  Converged
  * problems drop out; the others continue.  The launch shape (threads per
- * CTA, CTAs per SM, rows per tile) is chosen at init by timing candidates.
+ * CTA, CTAs per SM, rows per tile) is chosen at init by timing candidates;
+ * the launch sequence of one contour integration is captured once as a CUDA
+ * graph (per inner tolerance) and replayed every outer iteration.
  *
  * Blocks are DEVICE complex double, rows of all problems concatenated in
  * problem order: problem p's rows start at off_p = n_0 + ... + n_{p-1}, and
@@ -341,6 +343,8 @@ typedef struct {
   double max_res;              /* largest eq. (res) residual returned         */
   double inner_res;            /* largest relative inner residual, last filter */
   double t_filter_ms, t_rr_ms, t_total_ms, t_autotune_ms;
+  int32_t graph;               /* 1: the contour integration ran as a replayed
+                                  CUDA graph of its launch sequence          */
 } feast_nh_batch_info;
 
 /* Creates the batch: per-problem transposed CSR (for the ^H solves),

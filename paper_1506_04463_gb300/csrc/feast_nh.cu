@@ -1285,6 +1285,11 @@ struct feast_nh_batch {
   double t_autotune = 0;
   int krylov_its = 0, refine_steps = 0, inner_fail = 0;
   double inner_res = 0;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // filter launch sequence (first / later tolerance)
+  cudaStream_t gs = nullptr;                      // private stream the sequence is captured and replayed on
+  cudaEvent_t gev[2] = {nullptr, nullptr};        // ordering with the caller's stream
+  bool graph_ok = true;                           // stream capture of the sequence available
+  int graph_used = 0;
 };
 
 namespace {
@@ -1347,6 +1352,57 @@ void batch_filter_run(feast_nh_batch *b, double tol, int nsteps, int kmax) {
   const cudaError_t e = batch_fp32(b) ? batch_filter_launch<float>(b->L, b->grid, b->threads, b->s)
                                       : batch_filter_launch<double>(b->L, b->grid, b->threads, b->s);
   BCK(e);
+}
+
+// The launch sequence of one contour integration (resets of the barrier, the
+// counters and the statistics, the cooperative kernel, the read-back of the
+// statistics and the error word into pinned host memory) captured once as a
+// CUDA graph per tolerance and replayed each outer iteration.  If the stream
+// capture is not available the same sequence is launched directly.
+void batch_filter_iteration(feast_nh_batch *b, int which, double tol) {
+  // the caller's stream may be the legacy default stream, which cannot be
+  // captured: the sequence runs on the batch's own stream, ordered by events
+  BCK(cudaEventRecord(b->gev[0], b->s));
+  BCK(cudaStreamWaitEvent(b->gs, b->gev[0], 0));
+  cudaStream_t s = b->gs;
+  auto enqueue = [&]() -> cudaError_t {
+    b->L.ntiles = b->ntiles;
+    b->L.tol = tol;
+    b->L.nsteps = b->o.inner_max;
+    b->L.kmax = b->o.krylov_max;
+    cudaError_t e = batch_fp32(b) ? batch_filter_launch<float>(b->L, b->grid, b->threads, s)
+                                  : batch_filter_launch<double>(b->L, b->grid, b->threads, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->h_stats, b->L.stats, sizeof(BatchStats), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_err, b->L.err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    return e;
+  };
+  if (!b->gexec[which] && b->graph_ok) {
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    const cudaError_t e1 = ok ? enqueue() : cudaErrorUnknown;
+    const cudaError_t e2 = ok ? cudaStreamEndCapture(s, &g) : cudaErrorUnknown;
+    ok = ok && e1 == cudaSuccess && e2 == cudaSuccess && g;
+    if (ok && cudaGraphInstantiate(&b->gexec[which], g, 0) != cudaSuccess) {
+      b->gexec[which] = nullptr;
+      ok = false;
+    }
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+      b->graph_ok = false;
+      cudaGetLastError();  // a refused capture leaves no error behind
+    }
+  }
+  if (b->gexec[which]) {
+    BCK(cudaGraphLaunch(b->gexec[which], s));
+    note_launch();
+    b->graph_used = 1;
+  } else {
+    BCK(enqueue());
+    b->graph_used = 0;
+  }
+  BCK(cudaEventRecord(b->gev[1], s));
+  BCK(cudaStreamWaitEvent(b->s, b->gev[1], 0));
 }
 
 // Project autotuner: times the persistent launch (three Krylov iterations of
@@ -1413,6 +1469,14 @@ void batch_destroy_impl(feast_nh_batch *b) {
     if (e) cudaEventDestroy(e);
   for (auto &e : b->ev_rr)
     if (e) cudaEventDestroy(e);
+  for (auto &g : b->gexec)
+    if (g) cudaGraphExecDestroy(g);
+  for (auto &e : b->gev)
+    if (e) cudaEventDestroy(e);
+  if (b->gs) {
+    cudaStreamSynchronize(b->gs);
+    cudaStreamDestroy(b->gs);
+  }
   delete b;
 }
 
@@ -1445,6 +1509,8 @@ feast_nh_status feast_nh_batch_init(feast_nh_batch **out, int32_t nprob, const f
     b->iters.assign(nprob, 0);
     b->mfound.assign(nprob, 0);
     for (auto &e : b->ev) BCK(cudaEventCreateWithFlags(&e, cudaEventDefault));
+    for (auto &e : b->gev) BCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    BCK(cudaStreamCreateWithFlags(&b->gs, cudaStreamNonBlocking));
     // per-problem contexts (Rayleigh-Ritz workspace, transposed CSR, nodes)
     feast_nh_opts ro = b->o;
     ro.inner_kind = FEAST_NH_INNER_BANDED;
@@ -1590,9 +1656,7 @@ feast_nh_status feast_nh_batch_solve(feast_nh_batch *b, const void *Y0, const vo
       // the first outer iteration only supplies the start subspace of the
       // second: its shifted solves stop at a relative residual of 1e-2
       const double tol_it = it == 1 ? std::fmax(b->o.inner_tol, 1e-2) : b->o.inner_tol;
-      batch_filter_run(b, tol_it, b->o.inner_max, b->o.krylov_max);
-      BCK(cudaMemcpyAsync(b->h_stats, b->L.stats, sizeof(BatchStats), cudaMemcpyDeviceToHost, s));
-      BCK(cudaMemcpyAsync(b->h_err, b->L.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+      batch_filter_iteration(b, it == 1 ? 0 : 1, tol_it);
       BCK(cudaEventRecord(b->ev[2], s));
       // Rayleigh-Ritz of every active problem on its own stream, concurrently
       std::vector<std::thread> th;
@@ -1690,6 +1754,7 @@ feast_nh_status feast_nh_batch_solve(feast_nh_batch *b, const void *Y0, const vo
       info->t_rr_ms = t_rr;
       info->t_total_ms = tot;
       info->t_autotune_ms = b->t_autotune;
+      info->graph = b->graph_used;
     }
     if (nconv < np) {
       b->err = "some problems did not converge within max_iter outer iterations";

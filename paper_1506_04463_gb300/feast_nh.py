@@ -61,7 +61,7 @@ class BatchInfo(C.Structure):
                 ("krylov_iterations", C.c_int32), ("refine_steps", C.c_int32), ("threads", C.c_int32),
                 ("tile_rows", C.c_int32), ("grid", C.c_int32), ("max_res", C.c_double), ("inner_res", C.c_double),
                 ("t_filter_ms", C.c_double), ("t_rr_ms", C.c_double), ("t_total_ms", C.c_double),
-                ("t_autotune_ms", C.c_double)]
+                ("t_autotune_ms", C.c_double), ("graph", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

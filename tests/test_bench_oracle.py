@@ -28,3 +28,20 @@ def test_parallel_node_solvers_match_serial_oracle():
     assert ph["total_s"] > 0 and ph["factor_s"] > 0
     e = bench.per_pair_errors(par["lam"], par["res"], ser)
     assert e["max_rel_err"] == 0.0 and len(e["rel_err"]) == 30
+
+
+def test_reference_arm_line():
+    # bench.py --impl reference on a small grid: complete oracle solves, the
+    # base contract's keys, and the cpu_baseline / e2e objects of this arm
+    import argparse
+    import bench
+    args = argparse.Namespace(N=20, steps=1, warmup=0, impl="reference")
+    line = bench.run_reference(args, 0, 1)
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "cpu_baseline", "e2e", "config"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps_timed"] == 1
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    assert line["cpu_baseline"]["per_phase_s"]["total_s"] > 0

@@ -49,6 +49,7 @@ def test_batch_matches_oracle(family, prec):
     inf = out["info"]
     assert inf["converged_problems"] == len(bw.A) and inf["inner_fail"] == 0
     assert inf["threads"] > 0 and inf["tile_rows"] > 0 and inf["grid"] > 0 and inf["krylov_iterations"] > 0
+    assert inf["graph"] == 1  # the contour integration replayed as a CUDA graph
     for p, A in enumerate(bw.A):
         _check_problem(A, bw.contours[p], out["problems"][p], refs[p])
         assert abs(out["problems"][p]["iterations"] - refs[p]["iterations"]) <= 2
