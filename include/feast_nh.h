@@ -80,6 +80,7 @@ typedef struct {
 enum { FEAST_NH_INNER_BANDED = 0, FEAST_NH_INNER_BICGSTAB = 1, FEAST_NH_INNER_FGMRES = 2 };
 enum { FEAST_NH_PRECOND_NONE = 0, FEAST_NH_PRECOND_JACOBI = 1, FEAST_NH_PRECOND_LEARNED = 2 };
 enum { FEAST_NH_PREC_FP64 = 0, FEAST_NH_PREC_FP32_IR = 1 };
+enum { FEAST_NH_PROJ_FP64 = 0, FEAST_NH_PROJ_TENSOR = 1 };
 enum { FEAST_NH_PROBLEM_GENERAL = 0, FEAST_NH_PROBLEM_COMPLEX_SYMMETRIC = 1 };
 
 /* Options.  eps, eta, mu: eq. (res), eq. (resize), Sec. 2.7.  inner_tol is
@@ -103,6 +104,12 @@ typedef struct {
   int32_t krylov_restart; /* 30: FGMRES restart length (<= 64)              */
   int32_t precond;    /* FGMRES right preconditioner: FEAST_NH_PRECOND_JACOBI
                          (default), _NONE, or _LEARNED (feast_nh_set_network) */
+  int32_t projection; /* FEAST_NH_PROJ_TENSOR (default): the n x m^2 products
+                         of the Rayleigh-Ritz step (B_Q, A_U, B_U of steps 2.a
+                         and 4.a, U and Y of eq. uu and step 4.d) on the
+                         tensor cores as exact products of integer digits
+                         (FP64-accurate, see feast_nh_gram); FEAST_NH_PROJ_FP64:
+                         FP64 arithmetic on the CUDA cores                  */
 } feast_nh_opts;
 
 /* Per-call record (host).  Times are CUDA-event milliseconds on the stream. */
@@ -263,6 +270,31 @@ feast_nh_status feast_nh_multishift_spmm(feast_nh_ctx *ctx, const void *P, void 
  * eigensolver can be tested on its own.  Waits for the stream; a QR sweep
  * that does not converge returns FEAST_NH_ECUDA. */
 feast_nh_status feast_nh_small_eig(feast_nh_ctx *ctx, const void *M, int32_t m, void *lambda, void *V);
+
+/* G = X^H Y for device blocks X (n x mx) and Y (n x my), n = the context's
+ * size, row-major complex double with leading dimensions mx and my;
+ * G: mx x my, row-major (1 <= mx, my <= 128).  These are the projections of
+ * steps 2.a and 4.a of Fig. alg:three (B_Q = Q^H B Q, A_U = Uh^H A U,
+ * B_U = Uh^H B U).  method FEAST_NH_PROJ_TENSOR: every column is scaled by
+ * the power of two of its largest component, each value becomes a 55-bit
+ * fixed-point integer in eight signed 7-bit digits (exact in BF16), the 36
+ * digit-pair products of significance >= 2^-49 are summed exactly on the
+ * tensor cores (FP32 accumulators kept below 2^22) and in 64-bit integers,
+ * and the sum is rounded once to FP64: |error| <= about 2^-52 max|x| max|y|
+ * per term, and the result does not depend on the order of summation.
+ * FEAST_NH_PROJ_FP64: FP64 on the CUDA cores.  On ctx's stream, with ctx's
+ * workspace; waits for the stream.  Exposed so that the products can be
+ * tested on their own; feast_nh_solve/feast_nh_rr use opts.projection. */
+feast_nh_status feast_nh_gram(feast_nh_ctx *ctx, const void *X, const void *Y, int32_t mx, int32_t my, void *G,
+                              int32_t method);
+
+/* Z = X S for device blocks X (n x mx, leading dimension mx) and S (mx x mz,
+ * leading dimension mz), Z: n x mz (leading dimension mz); row-major complex
+ * double, 1 <= mx, mz <= 128: the block updates U = Q V Gamma^{-1/2}
+ * (eq. uu) and Y = U W (step 4.d).  Methods as for feast_nh_gram, with the
+ * scaling per row of X and per column of S.  Waits for the stream. */
+feast_nh_status feast_nh_block_product(feast_nh_ctx *ctx, const void *X, const void *S, int32_t mx, int32_t mz,
+                                       void *Z, int32_t method);
 
 /* Device error-word bits, as reported through the status codes. */
 enum { FEAST_NH_DEVERR_ZERO_PIVOT = 1, FEAST_NH_DEVERR_QR_NOCONV = 2, FEAST_NH_DEVERR_TIMEOUT = 16 };

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libfeast_nh.so")
-SOURCES = ["band.cu", "spmm.cu", "dense.cu", "rr.cu", "krylov.cu", "batch.cu", "net.cu", "fgmres.cu", "feast_nh.cu", "noalloc.cu"]
+SOURCES = ["band.cu", "spmm.cu", "dense.cu", "rr.cu", "krylov.cu", "batch.cu", "net.cu", "proj.cu", "fgmres.cu", "feast_nh.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

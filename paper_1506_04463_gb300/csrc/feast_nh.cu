@@ -57,6 +57,7 @@ struct feast_nh_ctx {
   double *part = nullptr;
   double *bynorm2 = nullptr;
   int *d_done = nullptr, *d_err = nullptr, *d_ext = nullptr;
+  int *d_fxy = nullptr;  // column exponent fields of the tensor-core projections
   double *d_maxrel = nullptr;
   cxd *BQ = nullptr, *gam = nullptr, *V = nullptr, *Vinv = nullptr, *S = nullptr, *Sh = nullptr, *AU = nullptr,
       *BU = nullptr, *BUinv = nullptr, *Mred = nullptr, *lam = nullptr, *lamc = nullptr, *W = nullptr,
@@ -529,6 +530,24 @@ void read_status(feast_nh_ctx *ctx) {
   ev_harvest(ctx->ev_resid);
 }
 
+// G = X^H Y (mx x my) and Z = X S over the n rows, on the tensor cores in
+// exact digit products (FP64-accurate) or in FP64 on the CUDA cores, as
+// opts.projection says.
+static void proj_gram(feast_nh_ctx *ctx, const cxd *X, int ldx, int mx, const cxd *Y, int ldy, int my, cxd *G) {
+  if (ctx->o.projection == FEAST_NH_PROJ_TENSOR)
+    gram_tc(X, ldx, mx, Y, ldy, my, ctx->n, G, reinterpret_cast<long long *>(ctx->gpart),
+            gram_tc_chunks(ctx->n, mx, my), ctx->d_fxy, ctx->d_err, ctx->s);
+  else
+    gram(X, ldx, mx, Y, ldy, my, ctx->n, G, ctx->gpart, ctx->gchunks, ctx->s);
+}
+static void proj_block(feast_nh_ctx *ctx, const cxd *X, int ldx, int mx, const cxd *S, int lds, int mz, cxd *Z,
+                       int ldz) {
+  if (ctx->o.projection == FEAST_NH_PROJ_TENSOR)
+    block_tc(X, ldx, mx, S, lds, mz, ctx->n, Z, ldz, ctx->d_err, ctx->s);
+  else
+    block_times_small(X, ldx, mx, S, lds, mz, ctx->n, Z, ldz, ctx->s);
+}
+
 // Steps 2-5 of Fig. alg:three.  Returns the new subspace size.
 int do_rr(feast_nh_ctx *ctx, const cxd *Q, const cxd *Qh, int m, cxd *Y, cxd *Yh) {
   const int n = ctx->n;
@@ -542,7 +561,7 @@ int do_rr(feast_nh_ctx *ctx, const cxd *Q, const cxd *Qh, int m, cxd *Y, cxd *Yh
     launch_spmm(ctx->B, nullptr, nullptr, Q, ctx->T1, m, nullptr, nullptr, s);
     BQq = ctx->T1;
   }
-  gram(Qh, m, m, BQq, m, m, n, ctx->BQ, ctx->gpart, ctx->gchunks, s);
+  proj_gram(ctx, Qh, m, m, BQq, m, m, ctx->BQ);
   // 3.a  B_Q = V Gamma V^^H ; 2.b spurious ; 3.b-3.c resize and sort
   small_eig(ctx->BQ, m, ctx->gam, ctx->V, ctx->swork, ctx->d_err, s);
   if (!cs) small_inv(ctx->V, m, ctx->Vinv, ctx->swork, ctx->d_err, s);
@@ -556,17 +575,17 @@ int do_rr(feast_nh_ctx *ctx, const cxd *Q, const cxd *Qh, int m, cxd *Y, cxd *Yh
     throw Fail{FEAST_NH_ESINGULAR};
   }
   // 3.d  U = Q V Gamma^{-1/2}, Uh = Qh Vh Gamma^{-H/2}        (eq. uu)
-  block_times_small(Q, m, m, ctx->S, m, mt, n, ctx->Uw, mt, s);
-  block_times_small(Qh, m, m, ctx->Sh, m, mt, n, ctx->Uhw, mt, s);
+  proj_block(ctx, Q, m, m, ctx->S, m, mt, ctx->Uw, mt);
+  proj_block(ctx, Qh, m, m, ctx->Sh, m, mt, ctx->Uhw, mt);
   // 4.a  A_U = Uh^H A U, B_U = Uh^H B U
   launch_spmm(ctx->A, nullptr, nullptr, ctx->Uw, ctx->T1, mt, nullptr, nullptr, s);
-  gram(ctx->Uhw, mt, mt, ctx->T1, mt, mt, n, ctx->AU, ctx->gpart, ctx->gchunks, s);
+  proj_gram(ctx, ctx->Uhw, mt, mt, ctx->T1, mt, mt, ctx->AU);
   const cxd *BUu = ctx->Uw;
   if (ctx->hasB) {
     launch_spmm(ctx->B, nullptr, nullptr, ctx->Uw, ctx->T2, mt, nullptr, nullptr, s);
     BUu = ctx->T2;
   }
-  gram(ctx->Uhw, mt, mt, BUu, mt, mt, n, ctx->BU, ctx->gpart, ctx->gchunks, s);
+  proj_gram(ctx, ctx->Uhw, mt, mt, BUu, mt, mt, ctx->BU);
   // 4.b  A_U W = B_U W Lambda via eig(B_U^{-1} A_U); Wh^H = W^{-1} B_U^{-1}
   small_inv(ctx->BU, mt, ctx->BUinv, ctx->swork, ctx->d_err, s);
   small_mm(ctx->BUinv, 0, ctx->AU, 0, ctx->Mred, mt, mt, mt, s);
@@ -580,8 +599,8 @@ int do_rr(feast_nh_ctx *ctx, const cxd *Q, const cxd *Qh, int m, cxd *Y, cxd *Yh
   // 4.c  rho_a(lambda)
   launch_rho(mt, ctx->ne, ctx->dz, ctx->dw, ctx->lam, ctx->rho, s);
   // 4.d  Y = U W, Yh = Uh Wh; column scale ||y_i|| = 1
-  block_times_small(ctx->Uw, mt, mt, ctx->W, mt, mt, n, Y, mt, s);
-  block_times_small(ctx->Uhw, mt, mt, ctx->Wh, mt, mt, n, Yh, mt, s);
+  proj_block(ctx, ctx->Uw, mt, mt, ctx->W, mt, mt, Y, mt);
+  proj_block(ctx, ctx->Uhw, mt, mt, ctx->Wh, mt, mt, Yh, mt);
   if (!cs) {
     int g = launch_colnorm2(Y, mt, mt, n, ctx->colp, s);
     launch_reduce_parts(ctx->colp, g, mt, ctx->cn, s);
@@ -626,6 +645,7 @@ void feast_nh_default_opts(feast_nh_opts *o) {
   o->krylov_max = 1000;
   o->krylov_restart = 30;
   o->precond = FEAST_NH_PRECOND_JACOBI;
+  o->projection = FEAST_NH_PROJ_TENSOR;
 }
 
 const char *feast_nh_strerror(feast_nh_status s) {
@@ -709,6 +729,7 @@ void init_ctx(feast_nh_ctx *ctx, const feast_nh_csr *A, const feast_nh_csr *B, c
     REQ(ctx->o.inner_kind != FEAST_NH_INNER_BICGSTAB || ctx->o.precision == FEAST_NH_PREC_FP64,
         "the BiCGStab inner solver runs in FP64");
     REQ(ctx->o.inner_max >= 1, "inner_max must be >= 1");
+    REQ(ctx->o.projection == FEAST_NH_PROJ_FP64 || ctx->o.projection == FEAST_NH_PROJ_TENSOR, "bad projection");
     REQ(ctx->o.precision == FEAST_NH_PREC_FP64 || ctx->o.precision == FEAST_NH_PREC_FP32_IR, "bad precision");
     REQ(ctx->o.problem == FEAST_NH_PROBLEM_GENERAL || ctx->o.problem == FEAST_NH_PROBLEM_COMPLEX_SYMMETRIC,
         "bad problem kind");
@@ -890,7 +911,8 @@ void init_ctx(feast_nh_ctx *ctx, const feast_nh_csr *A, const feast_nh_csr *B, c
     ctx->Wh = dalloc<cxd>(ctx, sm);
     ctx->swork = dalloc<cxd>(ctx, 3 * sm);
     ctx->gchunks = gram_chunks(n);
-    ctx->gpart = dalloc<cxd>(ctx, (size_t)ctx->gchunks * sm);
+    ctx->gpart = dalloc<cxd>(ctx, std::max((size_t)ctx->gchunks * sm, gram_tc_part_max(n)));
+    ctx->d_fxy = dalloc<int>(ctx, 2 * kMaxM0 * sizeof(int));
     ctx->gam = dalloc<cxd>(ctx, kMaxM0 * sizeof(cxd));
     ctx->lam = dalloc<cxd>(ctx, kMaxM0 * sizeof(cxd));
     ctx->lamc = dalloc<cxd>(ctx, kMaxM0 * sizeof(cxd));
@@ -1145,6 +1167,56 @@ feast_nh_status feast_nh_small_eig(feast_nh_ctx *ctx, const void *M, int32_t m, 
     CKC(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->s));
     small_eig((const cxd *)M, m, (cxd *)lambda, (cxd *)V, ctx->swork, ctx->d_err, ctx->s);
     check_launch(ctx, "small_eig");
+    CKC(cudaMemcpyAsync(ctx->h_small + 1, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+    CKC(cudaStreamSynchronize(ctx->s));
+    int herr = 0;
+    std::memcpy(&herr, ctx->h_small + 1, sizeof(int));
+    const feast_nh_status es = status_from_err(ctx, herr);
+    if (es != FEAST_NH_OK) return es;
+  } catch (const Fail &f) {
+    return f.st;
+  }
+  return FEAST_NH_OK;
+}
+
+feast_nh_status feast_nh_gram(feast_nh_ctx *ctx, const void *X, const void *Y, int32_t mx, int32_t my, void *G,
+                              int32_t method) {
+  if (!ctx) return FEAST_NH_EINVAL;
+  try {
+    REQ(X && Y && G && mx >= 1 && mx <= kMaxM0 && my >= 1 && my <= kMaxM0 &&
+            (method == FEAST_NH_PROJ_FP64 || method == FEAST_NH_PROJ_TENSOR),
+        "gram: bad arguments (1 <= mx, my <= 128, method FP64 or TENSOR)");
+    const int keep = ctx->o.projection;
+    ctx->o.projection = method;
+    CKC(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->s));
+    proj_gram(ctx, (const cxd *)X, mx, mx, (const cxd *)Y, my, my, (cxd *)G);
+    ctx->o.projection = keep;
+    check_launch(ctx, "gram");
+    CKC(cudaMemcpyAsync(ctx->h_small + 1, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+    CKC(cudaStreamSynchronize(ctx->s));
+    int herr = 0;
+    std::memcpy(&herr, ctx->h_small + 1, sizeof(int));
+    const feast_nh_status es = status_from_err(ctx, herr);
+    if (es != FEAST_NH_OK) return es;
+  } catch (const Fail &f) {
+    return f.st;
+  }
+  return FEAST_NH_OK;
+}
+
+feast_nh_status feast_nh_block_product(feast_nh_ctx *ctx, const void *X, const void *S, int32_t mx, int32_t mz,
+                                       void *Z, int32_t method) {
+  if (!ctx) return FEAST_NH_EINVAL;
+  try {
+    REQ(X && S && Z && mx >= 1 && mx <= kMaxM0 && mz >= 1 && mz <= kMaxM0 &&
+            (method == FEAST_NH_PROJ_FP64 || method == FEAST_NH_PROJ_TENSOR),
+        "block_product: bad arguments (1 <= mx, mz <= 128, method FP64 or TENSOR)");
+    const int keep = ctx->o.projection;
+    ctx->o.projection = method;
+    CKC(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->s));
+    proj_block(ctx, (const cxd *)X, mx, mx, (const cxd *)S, mz, mz, (cxd *)Z, mz);
+    ctx->o.projection = keep;
+    check_launch(ctx, "block_product");
     CKC(cudaMemcpyAsync(ctx->h_small + 1, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
     CKC(cudaStreamSynchronize(ctx->s));
     int herr = 0;

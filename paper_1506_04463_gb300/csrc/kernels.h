@@ -191,6 +191,16 @@ void launch_operator_loss(const CsrView &M, const CsrView &MH, int ne, int n, in
 void gram(const cxd *X, int ldx, int mx, const cxd *Y, int ldy, int my, int n, cxd *G, cxd *partial,
           int nchunks, cudaStream_t s);
 int gram_chunks(int n);
+// The same products on the tensor cores, FP64-accurate (exact digit products,
+// csrc/proj.cu).  FXY: 2 * kMaxM0 ints of scratch; part: at least
+// gram_tc_part_bytes(nchunks, mx, my) bytes; err: device error word.
+void gram_tc(const cxd *X, int ldx, int mx, const cxd *Y, int ldy, int my, int n, cxd *G, long long *part,
+             int nchunks, int *FXY, int *err, cudaStream_t s);
+int gram_tc_chunks(int n, int mx, int my);
+size_t gram_tc_part_bytes(int nchunks, int mx, int my);
+size_t gram_tc_part_max(int n);
+void block_tc(const cxd *X, int ldx, int mx, const cxd *S, int lds, int mz, int n, cxd *Z, int ldz, int *err,
+              cudaStream_t s);
 // Z (n x mz, ld ldz) = X (n x mx, ld ldx) * S (mx x mz, row-major, ld lds)
 void block_times_small(const cxd *X, int ldx, int mx, const cxd *S, int lds, int mz, int n, cxd *Z, int ldz,
                        cudaStream_t s);

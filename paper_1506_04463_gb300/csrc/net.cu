@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <cuda_bf16.h>
 #include "kernels.h"
+#include "tc.cuh"
 
 namespace {
 
@@ -36,73 +37,11 @@ constexpr int kSBO = (kK / 8) * 128; // bytes between 8-row groups: 4608
 constexpr int kAB = kTile * kK * 2;  // A tile bytes: 73728
 constexpr int kBB = kC * kK * 2;     // weight bytes: 18432
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// Shared-memory matrix descriptor (tcgen05): start address, leading and
-// stride byte offsets (all >> 4), fixed bits 46..48 = 0b001, no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;
-  return d;
-}
-
-// Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
-// (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at
-// bits 24-28.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kC >> 3) << 17) |
-                            ((uint32_t)(kTile >> 4) << 24);
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-// Bounded wait on an mbarrier phase; false if it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase) {
-  const uint32_t a = smem_u32(bar);
-  for (long long it = 0; it < (1ll << 26); ++it) {
-    uint32_t done = 0;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(phase)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void tc_commit(uint64_t *bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-// 32 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tc_ld32(uint32_t taddr, float *v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
-}
+using tc::smem_u32;
+using tc::smem_desc;
+using tc::mbar_init;
+using tc::mbar_wait;
+constexpr uint32_t kIdesc = tc::idesc_bf16(kTile, kC);
 
 // byte offset of element (row, k) in a canonical K-major no-swizzle operand
 __device__ __forceinline__ int canon_off(int row, int k) {
@@ -181,8 +120,9 @@ __global__ void __launch_bounds__(128, 2) k_conv3x3_tc(const __nv_bfloat16 *__re
       const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
 #pragma unroll
       for (int s = 0; s < kK / 16; ++s)
-        tc_mma(tmem, smem_desc(a0 + s * 2 * kLBO, kLBO, kSBO), smem_desc(b0 + s * 2 * kLBO, kLBO, kSBO), s > 0);
-      tc_commit(bar);
+        tc::mma(tmem, smem_desc(a0 + s * 2 * kLBO, kLBO, kSBO), smem_desc(b0 + s * 2 * kLBO, kLBO, kSBO), kIdesc,
+                s > 0);
+      tc::commit(bar);
     }
     // the CTA agrees on the outcome of the bounded wait, so that every thread
     // takes the same path through the barriers below
@@ -195,7 +135,7 @@ __global__ void __launch_bounds__(128, 2) k_conv3x3_tc(const __nv_bfloat16 *__re
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     // ---- epilogue: warp w holds rows (pixels) 32w .. 32w+31 ----
     float v[32];
-    tc_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
+    tc::ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
     if (live) {
       if (bias) {
 #pragma unroll

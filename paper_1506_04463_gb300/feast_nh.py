@@ -21,6 +21,7 @@ R64, C64 = 0, 1
 INNER_BANDED, INNER_BICGSTAB, INNER_FGMRES = 0, 1, 2
 PRECOND_NONE, PRECOND_JACOBI, PRECOND_LEARNED = 0, 1, 2
 PREC_FP64, PREC_FP32_IR = 0, 1
+PROJ_FP64, PROJ_TENSOR = 0, 1
 PROBLEM_GENERAL, PROBLEM_COMPLEX_SYMMETRIC = 0, 1
 
 
@@ -39,7 +40,8 @@ class Opts(C.Structure):
     _fields_ = [("eps", C.c_double), ("eta", C.c_double), ("mu", C.c_double), ("inner_tol", C.c_double),
                 ("max_iter", C.c_int32), ("inner_max", C.c_int32), ("inner_kind", C.c_int32),
                 ("precision", C.c_int32), ("problem", C.c_int32), ("timing", C.c_int32),
-                ("krylov_max", C.c_int32), ("krylov_restart", C.c_int32), ("precond", C.c_int32)]
+                ("krylov_max", C.c_int32), ("krylov_restart", C.c_int32), ("precond", C.c_int32),
+                ("projection", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -74,7 +76,8 @@ EXPORTS = ["feast_nh_default_opts", "feast_nh_init", "feast_nh_filter", "feast_n
            "feast_nh_batch_destroy", "feast_nh_batch_last_error", "feast_nh_multishift_spmm", "feast_nh_net_create",
            "feast_nh_net_set_params", "feast_nh_net_get_params", "feast_nh_net_forward", "feast_nh_net_train_step",
            "feast_nh_net_destroy", "feast_nh_net_last_error", "feast_nh_set_network", "feast_nh_learned_pairs",
-           "feast_nh_operator_loss", "feast_nh_net_backward"]
+           "feast_nh_operator_loss", "feast_nh_net_backward", "feast_nh_gram",
+           "feast_nh_block_product"]
 
 _lib = None
 
@@ -104,6 +107,8 @@ def lib():
     L.feast_nh_nodes.argtypes = [C.POINTER(ContourS), C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.feast_nh_multishift_residual.argtypes = [vp, vp, vp, vp, vp, i32, i32]
     L.feast_nh_small_eig.argtypes = [vp, vp, i32, vp, vp]
+    L.feast_nh_gram.argtypes = [vp, vp, vp, i32, i32, vp, i32]
+    L.feast_nh_block_product.argtypes = [vp, vp, vp, i32, i32, vp, i32]
     L.feast_nh_multishift_spmm.argtypes = [vp, vp, vp, i32, i32]
     L.feast_nh_inject_device_error.argtypes = [vp, C.c_uint32]
     L.feast_nh_multishift_residual_noalloc.argtypes = [C.POINTER(Csr), C.POINTER(Csr), C.POINTER(ContourS), vp, vp,
@@ -143,7 +148,7 @@ def lib():
     L.feast_nh_kernel_launches.restype = C.c_uint64
     for f in ("feast_nh_init", "feast_nh_filter", "feast_nh_rr", "feast_nh_solve", "feast_nh_nodes",
               "feast_nh_multishift_residual", "feast_nh_small_eig", "feast_nh_inject_device_error",
-              "feast_nh_multishift_spmm"):
+              "feast_nh_multishift_spmm", "feast_nh_gram", "feast_nh_block_product"):
         getattr(L, f).restype = i32
     _lib = L
     return L
@@ -364,6 +369,34 @@ class FeastNH:
         st = lib().feast_nh_small_eig(self.h, _ptr(Mc), m, _ptr(lam), _ptr(V))
         self._check(st, "feast_nh_small_eig")
         return lam, V
+
+    def gram(self, X, Y, method=None):
+        """G = X^H Y (X: n x mx, Y: n x my device tensors) by the library's
+        projection kernels; method PROJ_TENSOR (default) or PROJ_FP64."""
+        Xc = X.to(torch.complex128).contiguous()
+        Yc = Y.to(torch.complex128).contiguous()
+        if Xc.shape[0] != self.n or Yc.shape[0] != self.n:
+            raise ValueError("gram: X and Y need n rows")
+        mx, my = Xc.shape[1], Yc.shape[1]
+        G = torch.empty((mx, my), dtype=torch.complex128, device=Xc.device)
+        st = lib().feast_nh_gram(self.h, _ptr(Xc), _ptr(Yc), mx, my, _ptr(G),
+                                 PROJ_TENSOR if method is None else method)
+        self._check(st, "feast_nh_gram")
+        return G
+
+    def block_product(self, X, S, method=None):
+        """Z = X S (X: n x mx, S: mx x mz device tensors) by the library's
+        block-update kernels; method PROJ_TENSOR (default) or PROJ_FP64."""
+        Xc = X.to(torch.complex128).contiguous()
+        Sc = S.to(torch.complex128, device=Xc.device).contiguous()
+        if Xc.shape[0] != self.n or Sc.shape[0] != Xc.shape[1]:
+            raise ValueError("block_product: X must be n x mx and S mx x mz")
+        mx, mz = Sc.shape
+        Z = torch.empty((self.n, mz), dtype=torch.complex128, device=Xc.device)
+        st = lib().feast_nh_block_product(self.h, _ptr(Xc), _ptr(Sc), mx, mz, _ptr(Z),
+                                          PROJ_TENSOR if method is None else method)
+        self._check(st, "feast_nh_block_product")
+        return Z
 
     def learned_pairs(self, R, N, kappa=1.0, features=()):
         """(inputs, targets) for the network from exact solves of R (n x m):
