@@ -388,7 +388,7 @@ class FeastNH:
         """Z = X S (X: n x mx, S: mx x mz device tensors) by the library's
         block-update kernels; method PROJ_TENSOR (default) or PROJ_FP64."""
         Xc = X.to(torch.complex128).contiguous()
-        Sc = S.to(torch.complex128, device=Xc.device).contiguous()
+        Sc = S.to(device=Xc.device, dtype=torch.complex128).contiguous()
         if Xc.shape[0] != self.n or Sc.shape[0] != Xc.shape[1]:
             raise ValueError("block_product: X must be n x mx and S mx x mz")
         mx, mz = Sc.shape
