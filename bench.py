@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--workload", choices=["convdiff", "batched", "kernels"], default="convdiff",
                    help="convdiff: the 300 x 300 convection-diffusion solve (default); batched: 64 random sparse "
                         "problems of uneven size in one batched solve")
+    p.add_argument("--only", default="",
+                   help="--workload kernels: comma list of spmm_f32, conv, batch, proj (default: all)")
     p.add_argument("--nprob", type=int, default=64)
     p.add_argument("--nmax", type=int, default=200000)
     p.add_argument("--max-iter", type=int, default=30, help="outer iteration cap of the batched solve")
@@ -149,7 +151,9 @@ def run_ours(args, rank, world, local_rank):
     prec = F.PREC_FP32_IR if args.form == "chosen" else F.PREC_FP64
     stream = torch.cuda.current_stream(dev)
     extra = {} if args.inner_tol is None else {"inner_tol": args.inner_tol}
-    ctx = F.FeastNH(wk.A, None, wk.contour, wk.m0, device=dev, precision=prec, timing=1, **extra)
+    # the chosen form takes the tensor-core Rayleigh-Ritz products, the plain form FP64 throughout
+    proj = F.PROJ_TENSOR if args.form == "chosen" else F.PROJ_FP64
+    ctx = F.FeastNH(wk.A, None, wk.contour, wk.m0, device=dev, precision=prec, projection=proj, timing=1, **extra)
     Y0 = torch.from_numpy(np.ascontiguousarray(wk.Y0)).to(dev)
     Yh0 = torch.from_numpy(np.ascontiguousarray(wk.Yh0)).to(dev)
     # L2 flush buffer (256 MB > 129 MB L2), written between timed steps
@@ -250,7 +254,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- plain FP64 form, same workload, one solve ----
     plain = None
     if args.form == "chosen" and not args.no_plain:
-        ctxp = F.FeastNH(wk.A, None, wk.contour, wk.m0, device=dev, precision=F.PREC_FP64)
+        ctxp = F.FeastNH(wk.A, None, wk.contour, wk.m0, device=dev, precision=F.PREC_FP64, projection=F.PROJ_FP64)
         ctxp.solve(Y0, Yh0)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -282,10 +286,12 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_max / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "c64 solves + c128 refinement/RR" if prec == F.PREC_FP32_IR else "c128",
+        "dtype": ("c64 solves + c128 refinement/RR; RR products as exact bf16-digit tensor-core sums"
+                  if prec == F.PREC_FP32_IR else "c128"),
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "nnz": int(wk.A.nnz), "m0": m, "ne": ne,
-                   "form": "chosen: FP32 banded LU + FP64 iterative refinement" if prec == F.PREC_FP32_IR
+                   "form": ("chosen: FP32 banded LU + FP64 iterative refinement; Rayleigh-Ritz products on the tensor cores "
+                            "(FP64-accurate exact digit products)") if prec == F.PREC_FP32_IR
                    else "plain FP64 banded LU", "parallelism": f"replicas x{world}",
                    "l2": "256 MB buffer written between timed steps; working set > L2"},
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "spmm": spmm, "spmm_f32": spmm_f32,
@@ -351,7 +357,8 @@ def e2e_measure(args, wk, dev, prec, F, torch):
         t0 = time.perf_counter()
         d_rp, d_ci, d_va = rp.to(dev, non_blocking=True), ci.to(dev, non_blocking=True), va.to(dev, non_blocking=True)
         dY0, dYh0 = Y0.to(dev, non_blocking=True), Yh0.to(dev, non_blocking=True)
-        ctx = F.FeastNH((d_rp, d_ci, d_va, F.R64, n, A.nnz), None, wk.contour, m0, device=dev, precision=prec)
+        ctx = F.FeastNH((d_rp, d_ci, d_va, F.R64, n, A.nnz), None, wk.contour, m0, device=dev, precision=prec,
+                        projection=F.PROJ_TENSOR if prec == F.PREC_FP32_IR else F.PROJ_FP64)
         out = ctx.solve(dY0, dYh0)
         mm = out["m"]
         h_lam[:mm].copy_(out["lam"], non_blocking=True)
@@ -617,7 +624,8 @@ def run_batched(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     prec = F.PREC_FP32_IR if args.form == "chosen" else F.PREC_FP64
     t0 = time.perf_counter()
-    b = F.FeastBatch(bw.A, bw.contours, bw.m0, device=dev, precision=prec, max_iter=args.max_iter)
+    b = F.FeastBatch(bw.A, bw.contours, bw.m0, device=dev, precision=prec, max_iter=args.max_iter,
+                     projection=F.PROJ_TENSOR if args.form == "chosen" else F.PROJ_FP64)
     t_init = time.perf_counter() - t0
     log(f"batch init (transposes, workspace, launch-shape tuner): {t_init:.1f} s")
     Y0 = torch.from_numpy(bw.Y0).to(dev)
@@ -699,12 +707,63 @@ def run_kernels(args, rank, world, local_rank):
     peaks = load_peaks()
     hbm = peaks.get("hbm_gbs", 6786.6)
     res = {}
+    only = set(args.only.split(",")) if args.only else {"spmm_f32", "conv", "batch", "proj"}
     # FP32 multi-shift SpMM
     wk = wl.config2(N=args.N)
-    ctx = F.FeastNH(wk.A, None, wk.contour, wk.m0, device=dev, precision=F.PREC_FP32_IR)
-    res["spmm_f32"] = spmm_f32_measure(ctx, wk, dev, F, torch, peaks, reps=10)
-    ctx.close()
-    # one convolution layer (forward of a 1-layer network: conv + bias)
+    if "spmm_f32" in only or "proj" in only:
+        ctx = F.FeastNH(wk.A, None, wk.contour, wk.m0, device=dev, precision=F.PREC_FP32_IR)
+        if "spmm_f32" in only:
+            res["spmm_f32"] = spmm_f32_measure(ctx, wk, dev, F, torch, peaks, reps=10)
+        if "proj" in only:
+            res["proj"] = proj_measure(ctx, wk.m0, dev, F, torch, reps=10)
+        ctx.close()
+    if "conv" in only:
+        res["conv3x3_tc"] = conv_measure(dev, F, torch, stream)
+    if "batch" in only:
+        # batched contour integration, one refinement step on a fixed input
+        bw = wl.config4(nprob=8, nmin=5000, nmax=20000, seed=3, workers=host_cores())
+        b = F.FeastBatch(bw.A, bw.contours, bw.m0, device=dev, precision=F.PREC_FP32_IR, max_iter=2)
+        t0 = time.perf_counter()
+        out = b.solve(torch.from_numpy(bw.Y0).to(dev), torch.from_numpy(bw.Yh0).to(dev))
+        torch.cuda.synchronize()
+        res["batch"] = {"problems": 8, "sum_n": int(sum(a.shape[0] for a in bw.A)), "outer_iterations": 2,
+                        "wall_s": round(time.perf_counter() - t0, 3), "info": out["info"]}
+        b.close()
+    if rank != 0:
+        return None
+    return {"workload": "kernels", "hbm_gbs_measured_peak": hbm, "results": res}
+
+
+def proj_measure(ctx, m, dev, F, torch, reps=10):
+    """The Rayleigh-Ritz products at the solve's shapes (n x m blocks, m x m
+    matrices): G = X^H Y and Z = X S on the tensor cores (exact digit
+    products) and in FP64 on the CUDA cores, CUDA events per call through the
+    C ABI (each call ends with a stream synchronisation)."""
+    g = torch.Generator(device=dev).manual_seed(0)
+    n = ctx.n
+    X = torch.randn((n, m), dtype=torch.complex128, device=dev, generator=g)
+    Y = torch.randn((n, m), dtype=torch.complex128, device=dev, generator=g)
+    S = torch.randn((m, m), dtype=torch.complex128, device=dev, generator=g)
+    out = {"n": n, "m": m}
+    for meth, name in ((F.PROJ_TENSOR, "tensor"), (F.PROJ_FP64, "fp64")):
+        for op, f in (("gram", lambda: ctx.gram(X, Y, meth)), ("block", lambda: ctx.block_product(X, S, meth))):
+            for _ in range(3):
+                f()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(ctx.stream)
+            for _ in range(reps):
+                f()
+            e1.record(ctx.stream)
+            torch.cuda.synchronize()
+            out[f"{op}_{name}_ms"] = round(e0.elapsed_time(e1) / reps, 4)
+    G1, G2 = ctx.gram(X, Y, F.PROJ_TENSOR), ctx.gram(X, Y, F.PROJ_FP64)
+    out["gram_rel_diff"] = float(torch.linalg.norm(G1 - G2) / torch.linalg.norm(G2))
+    return out
+
+
+def conv_measure(dev, F, torch, stream):
+    """One convolution layer (forward of a 1-layer network: conv + bias)."""
     N, nimg = 64, 512
     net = F.Net(1, N, nimg, device=dev)
     rng = np.random.default_rng(0)
@@ -721,21 +780,9 @@ def run_kernels(args, rank, world, local_rank):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps  # includes the FP32 -> BF16 input conversion and the output copy
     flops = 2.0 * nimg * N * N * 32 * 288
-    res["conv3x3_tc"] = {"kernel": "k_conv3x3_tc", "images": nimg, "grid": N, "ms_per_forward": round(ms, 4),
-                         "tflops_incl_conversions": round(flops / (ms / 1e3) / 1e12, 2)}
     net.close()
-    # batched contour integration, one refinement step on a fixed input
-    bw = wl.config4(nprob=8, nmin=5000, nmax=20000, seed=3, workers=host_cores())
-    b = F.FeastBatch(bw.A, bw.contours, bw.m0, device=dev, precision=F.PREC_FP32_IR, max_iter=2)
-    t0 = time.perf_counter()
-    out = b.solve(torch.from_numpy(bw.Y0).to(dev), torch.from_numpy(bw.Yh0).to(dev))
-    torch.cuda.synchronize()
-    res["batch"] = {"problems": 8, "sum_n": int(sum(a.shape[0] for a in bw.A)), "outer_iterations": 2,
-                    "wall_s": round(time.perf_counter() - t0, 3), "info": out["info"]}
-    b.close()
-    if rank != 0:
-        return None
-    return {"workload": "kernels", "hbm_gbs_measured_peak": hbm, "results": res}
+    return {"kernel": "k_conv3x3_tc", "images": nimg, "grid": N, "ms_per_forward": round(ms, 4),
+            "tflops_incl_conversions": round(flops / (ms / 1e3) / 1e12, 2)}
 
 
 def main():
