@@ -173,6 +173,43 @@ def laplace3d_cap(L: int, layers: int, seed_cap: int = 0, seed_b: int = 1):
     return A, B
 
 
+def nearest_circle(A, B, target: complex, k_lo: int, k_hi: int, nev: int):
+    """Circle centred at `target` holding k_lo..k_hi eigenvalues of the pencil
+    (A, B) (input construction only: ARPACK shift-invert, the `nev` eigenvalues
+    nearest the target).  Radius halfway across the widest relative gap among
+    the sorted distances; every eigenvalue inside is among the computed ones.
+    Returns (contour, eigenvalues inside)."""
+    import scipy.sparse.linalg as spla
+    ev = spla.eigs(A.tocsc(), k=nev, M=None if B is None else B.tocsc(), sigma=target, which="LM",
+                   return_eigenvectors=False, tol=1e-13)
+    d = np.sort(np.abs(ev - target))
+    best = None
+    for k in range(k_lo, min(k_hi, nev - 1) + 1):
+        r = 0.5 * (d[k - 1] + d[k])
+        gap = (d[k] - d[k - 1]) / r
+        if best is None or gap > best[0]:
+            best = (gap, r)
+    r = best[1]
+    con = Contour(0, complex(target), r)
+    return con, np.sort_complex(ev[np.abs(ev - target) <= r])
+
+
+def config3(L: int = 64, layers: int = 8, m0: int = 128, ne: int = 16, target: complex = 0.35 - 0.1j,
+            k_lo: int = 40, k_hi: int = 60, nev: int = 80) -> Workload:
+    """Generalized complex-symmetric problem: 7-point Laplacian on L^3 plus an
+    absorbing potential i*U(-0.5, 0) on the outer `layers` layers, B = diag
+    U(1, 2); a circle around k_lo..k_hi eigenvalues nearest `target`; complex
+    start block (N(0,1) + iN(0,1))/sqrt(2), Yh0 = conj(Y0) (Sec. 2.4).  The
+    full size is L = 64, layers = 8, m0 = 128, 40-60 eigenvalues; L = 16,
+    layers = 2 is the scaled family member a banded solver reaches."""
+    A, B = laplace3d_cap(L, layers)
+    con, ev = nearest_circle(A, B, target, k_lo, k_hi, nev)
+    con = Contour(0, con.center, con.r, ne=ne)
+    Y0 = start_block(A.shape[0], m0, 0, complex_=True)
+    return Workload(f"laplace3d_cap_{L}", A, B, con, m0, Y0, Y0.conj(), "complex_symmetric", exact=ev,
+                    meta={"L": L, "layers": layers})
+
+
 def random_sparse(n: int, seed: int, nnz_row: int = 9, shift_max: float = 4.0) -> sp.csr_matrix:
     """Each row: the diagonal plus nnz_row-1 distinct random off-diagonal
     columns, values N(0, 1/9); then diagonal += U(0, shift_max)."""

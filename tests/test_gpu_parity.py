@@ -154,6 +154,26 @@ def test_complex_symmetric(mode):
     assert np.min(cosang) > 1 - 1e-9
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_config3_family_16cube(prec):
+    # scaled member of the generalized complex-symmetric workload (16^3, two
+    # absorbing layers, B diagonal; band 256): CUDA path vs oracle vs ARPACK
+    wk = wl.config3(L=16, layers=2, m0=32, ne=16, k_lo=16, k_hi=24, nev=40)
+    oo = OF.feast_nh(wk.A, wk.B, wk.contour, wk.m0, wk.Y0, wk.Yh0, problem="complex_symmetric")
+    ctx = make_ctx(wk, precision=prec, problem=F.PROBLEM_COMPLEX_SYMMETRIC)
+    out = ctx.solve(dev(wk.Y0), dev(wk.Yh0))
+    assert out["status"] == F.OK and out["m"] == oo["m"] == wk.exact.size
+    lam = host(out["lam"])
+    assert match_rel(lam, oo["lam"], 1e-3) < 1e-9
+    assert match_rel(lam, wk.exact, 1e-3) < 1e-9
+    invariants(wk, out)
+    X, Xh = host(out["X"]), host(out["Xh"])
+    cosang = np.abs(np.sum(Xh * X, axis=0)) / (np.linalg.norm(X, axis=0) * np.linalg.norm(Xh, axis=0))
+    assert np.min(cosang) > 1 - 1e-9
+    assert abs(out["info"]["iterations"] - oo["iterations"]) <= 2
+    ctx.close()
+
+
 def test_edge_cases():
     # m0 = 1 with one eigenvalue inside; ne = 3; ragged n
     A = sp.diags(np.linspace(1.0, 2.0, 37) + 0j).tocsr()

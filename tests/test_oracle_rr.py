@@ -157,6 +157,20 @@ def test_complex_symmetric_problem():
         assert np.max(np.abs(Xh.conj().T @ (B @ X) - np.eye(6))) < 1e-10
 
 
+def test_complex_symmetric_16cube_family_vs_arpack():
+    # the config-3 family at 16^3 with 2 absorbing layers (Sec. 2.4, the CSH
+    # stand-in): the oracle's eigenvalues inside the circle equal ARPACK's
+    # shift-invert eigenvalues of the same pencil, none missing
+    wk = wl.config3(L=16, layers=2, m0=32, ne=16, k_lo=16, k_hi=24, nev=40)
+    out = F.feast_nh(wk.A, wk.B, wk.contour, wk.m0, wk.Y0, wk.Yh0, problem="complex_symmetric")
+    assert out["converged"] and out["m"] == wk.exact.size >= 16
+    assert _match(out["lam"], wk.exact) < 1e-10
+    X, Xh = out["X"], out["Xh"]
+    assert np.max(np.abs(Xh.conj().T @ (wk.B @ X) - np.eye(out["m"]))) < 1e-10
+    cosang = np.abs(np.sum(Xh * X, axis=0)) / (np.linalg.norm(X, axis=0) * np.linalg.norm(Xh, axis=0))
+    assert np.min(cosang) > 1 - 1e-9                          # x^_i parallel to conj(x_i)
+
+
 def test_resize_on_rank_deficient_start():
     # Duplicate start columns make B_Q singular: the subspace is resized
     # (eq. resize) and the run still converges.
