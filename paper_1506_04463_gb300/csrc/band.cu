@@ -182,6 +182,33 @@ template <typename T> __device__ __forceinline__ T rcp_rn(T x);
 template <> __device__ __forceinline__ float rcp_rn<float>(float x) { return __frcp_rn(x); }
 template <> __device__ __forceinline__ double rcp_rn<double>(double x) { return __drcp_rn(x); }
 
+// conj(piv) / |piv|^2 for the panel's pivots (0 for a zero pivot).  FP32:
+// the pivot is scaled by the power of two 2^-floor(log2 max(|re|, |im|)),
+// formed from the exponent bits (exact), so that |piv|^2 of the scaled value
+// lies in [1, 32) and one hardware reciprocal (rcp.approx, relative error
+// below 2^-22) completes it; the FP32 factors are refined in FP64, and the
+// reciprocal sits on the serial chain of the panel.  FP64: the correctly
+// rounded reciprocal, with the same scaling by max(|re|, |im|).
+template <typename T> __device__ __forceinline__ cx<T> pivot_recip(cx<T> piv);
+template <> __device__ __forceinline__ cx<float> pivot_recip<float>(cx<float> piv) {
+  const float sc = fmaxf(fabsf(piv.re), fabsf(piv.im));
+  if (sc == 0.f) return mk<float>(0.f, 0.f);
+  const int e = min(max((__float_as_int(sc) >> 23) & 0xFF, 1), 253);
+  const float rs = __int_as_float((254 - e) << 23);  // 2^(127 - e)
+  const float ar = piv.re * rs, ai = piv.im * rs;
+  float rd;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rd) : "f"(ar * ar + ai * ai));
+  rd *= rs;
+  return mk<float>(ar * rd, -ai * rd);
+}
+template <> __device__ __forceinline__ cx<double> pivot_recip<double>(cx<double> piv) {
+  const double sc = fmax(fabs(piv.re), fabs(piv.im));
+  if (sc == 0.0) return mk<double>(0.0, 0.0);
+  const double rs = rcp_rn(sc), ar = piv.re * rs, ai = piv.im * rs;
+  const double rd = rcp_rn(ar * ar + ai * ai) * rs;
+  return mk<double>(ar * rd, -ai * rd);
+}
+
 // Register panel elimination with compile-time column indices: thread i holds
 // row i of the panel in row[]; prow_s is a double-buffered pivot row and
 // pinv_s the reciprocal of its pivot, formed once by the pivot thread.
@@ -196,16 +223,8 @@ __device__ __forceinline__ void panel_eliminate(cx<T> (&row)[NB], cx<T> (*prow_s
 #pragma unroll
         for (int q = p + 1; q < NB; ++q) pr[q] = row[q];
         const cx<T> piv = row[p];
-        const T sc = fmax(fabs(piv.re), fabs(piv.im));
-        if (sc == 0) {
-          atomicOr(err, DEVERR_ZERO_PIVOT);
-          pinv_s[p & 1] = mk<T>(0, 0);
-        } else {
-          // conj(piv) / |piv|^2 with the scale sc kept out of the squares
-          const T rs = rcp_rn(sc), ar = piv.re * rs, ai = piv.im * rs;
-          const T rd = rcp_rn(ar * ar + ai * ai) * rs;
-          pinv_s[p & 1] = mk<T>(ar * rd, -ai * rd);
-        }
+        if (piv.re == 0 && piv.im == 0) atomicOr(err, DEVERR_ZERO_PIVOT);
+        pinv_s[p & 1] = pivot_recip<T>(piv);
       }
       __syncthreads();
       if (own && i > p && i - p <= kl) {

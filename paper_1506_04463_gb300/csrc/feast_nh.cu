@@ -1070,6 +1070,10 @@ feast_nh_status feast_nh_solve(feast_nh_ctx *ctx, const void *Y0, const void *Yh
       mt = do_rr(ctx, ctx->Qw, ctx->Qhw, m, ctx->Yw, ctx->Yhw);
       CKC(cudaEventRecord(ctx->ev[3], s));
       read_status(ctx);
+      // Sec. 2.7 compares the next B_Q with these Ritz values; Ritz values
+      // from a filter that was not solved to inner_tol (the 1e-2 first pass,
+      // unless the banded FP64 factors met inner_tol anyway) are no reference
+      if (!(tol_it <= ctx->o.inner_tol || (banded(ctx) && ctx->h_small[0] <= ctx->o.inner_tol))) ctx->have_prev = 0;
       float a = 0, b = 0;
       cudaEventElapsedTime(&a, ctx->ev[1], ctx->ev[2]);
       cudaEventElapsedTime(&b, ctx->ev[2], ctx->ev[3]);
@@ -1734,13 +1738,14 @@ feast_nh_status feast_nh_batch_solve(feast_nh_batch *b, const void *Y0, const vo
       std::vector<std::thread> th;
       for (int p = 0; p < np; ++p) {
         if (!b->hp[p].active) continue;
-        th.emplace_back([b, p, &pst]() {
+        th.emplace_back([b, p, &pst, tol_it]() {
           feast_nh_ctx *c = b->ctx[p];
           try {
             if (cudaStreamWaitEvent(c->s, b->ev[2], 0) != cudaSuccess) throw Fail{FEAST_NH_ECUDA};
             const size_t o = b->hp[p].off * b->m0;
             const int mt = do_rr(c, b->Q + o, b->Qh + o, b->hp[p].m, b->Y + o, b->Yh + o);
             read_status(c);
+            if (tol_it > b->o.inner_tol) c->have_prev = 0;  // no spurious-test reference (Sec. 2.7)
             b->mt[p] = mt;
             b->conv[p] = c->h_st->conv;
             b->mfound[p] = c->h_st->m;
