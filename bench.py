@@ -234,9 +234,15 @@ def run_ours(args, rank, world, local_rank):
         avg = resid_ms / n_resid
         gbs = resid_bytes / (avg / 1e3) / 1e9
         hbm = peaks.get("hbm_gbs", 6786.6)
+        # FP64 work per launch: every (node, column) pair forms z_j x (4 FMA)
+        # and the real A's products (2 FMA per entry) on every row
+        resid_flops = ne * m * (8.0 * n + 4.0 * wk.A.nnz)
+        tf = resid_flops / (avg / 1e3) / 1e12
         spmm = {"kernel": "k_multishift_residual", "bound_note": "FP64 arithmetic (GB300 FP64 ~1 TFLOP/s)",
                 "achieved_gbs": round(gbs, 1), "peak_gbs": hbm, "frac_of_measured_hbm": round(gbs / hbm, 4),
                 "frac_of_8tbs": round(gbs / 8000.0, 4), "bytes_per_launch": resid_bytes,
+                "fp64_flops_per_launch": resid_flops, "achieved_fp64_tflops": round(tf, 3),
+                "frac_of_fp64_nominal": round(tf / 1.25, 4), "fp64_peak_note": "FP64 nominal 1.25 TFLOP/s",
                 "avg_launch_ms": round(avg, 3), "launches": n_resid}
     # FP32 multi-shift operator of the Krylov sweeps on the same matrix and
     # block shape (ne = 16 nodes x 64 columns): HBM-bound, 16-byte loads
