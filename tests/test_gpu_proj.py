@@ -10,6 +10,8 @@ tensor cores, in exact integer-digit products, against FP64 references:
   and within the FP64 kernels' own error;
 * columns whose scales span 10^-150 .. 10^150 and an all-zero column: the
   per-column power-of-two scaling keeps every entry's relative accuracy;
+* the Gram products do not depend on the order of summation (row
+  permutations give bit-identical results);
 * full solves with either method give the same Ritz pairs."""
 import numpy as np
 import pytest
@@ -66,6 +68,21 @@ def test_gram_tensor_accuracy(n, mx, my):
     assert np.all(np.abs(Gt - ref) <= bound + fp64)
     assert np.all(np.abs(Gf - ref) <= fp64)
     assert np.linalg.norm(Gt - ref) <= 1e-14 * np.linalg.norm(ref)
+    ctx.close()
+
+
+def test_gram_independent_of_summation_order():
+    # the digit products are summed exactly (integers) and rounded once, so
+    # permuting the rows of X and Y together (which moves them between the
+    # CTAs' row chunks) leaves G bit-identical; an FP summation would not
+    n, m = 50021, 64
+    rng = np.random.default_rng(5)
+    X, Y = _cplx(rng, n, m), _cplx(rng, n, m)
+    perm = rng.permutation(n)
+    ctx = _ctx(n)
+    G1 = host(ctx.gram(dev(X), dev(Y), F.PROJ_TENSOR))
+    G2 = host(ctx.gram(dev(X[perm]), dev(Y[perm]), F.PROJ_TENSOR))
+    assert np.array_equal(G1, G2)
     ctx.close()
 
 
