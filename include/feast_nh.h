@@ -296,6 +296,16 @@ feast_nh_status feast_nh_gram(feast_nh_ctx *ctx, const void *X, const void *Y, i
 feast_nh_status feast_nh_block_product(feast_nh_ctx *ctx, const void *X, const void *S, int32_t mx, int32_t mz,
                                        void *Z, int32_t method);
 
+/* Device workspace of contexts and batches comes from one stream-ordered
+ * memory pool per device, owned by the library (allocated in stream order on
+ * the context's stream at init, returned in stream order at destroy).  The
+ * pool keeps returned memory reserved, so a following init reuses it without
+ * cudaMalloc / cudaFree; this call gives the reserved, unused memory back to
+ * the driver (for example before other code needs the device memory).
+ * Memory of live contexts is not affected.  Returns FEAST_NH_ECUDA if a trim
+ * fails. */
+feast_nh_status feast_nh_release_memory(void);
+
 /* Device error-word bits, as reported through the status codes. */
 enum { FEAST_NH_DEVERR_ZERO_PIVOT = 1, FEAST_NH_DEVERR_QR_NOCONV = 2, FEAST_NH_DEVERR_TIMEOUT = 16 };
 

@@ -4,6 +4,7 @@
 // kernels of band.cu, spmm.cu, dense.cu and rr.cu.
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <thread>
 #include <cmath>
 #include <cstdio>
@@ -19,6 +20,54 @@ static std::atomic<uint64_t> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // CUDA-event pairs around launches of one kernel, harvested at sync points.
+// Workspace comes from one stream-ordered memory pool per device, owned by
+// the library, whose release threshold keeps freed memory reserved: a
+// destroyed context's workspace serves the next context without cudaMalloc /
+// cudaFree of gigabytes (the caching idea of PyTorch's allocator).
+// feast_nh_release_memory() hands the reserved memory back to the driver.
+// Without a pool (creation refused), plain cudaMalloc / cudaFree.
+namespace pool {
+constexpr int kMaxDev = 64;
+std::mutex mu;
+cudaMemPool_t p[kMaxDev] = {};
+bool tried[kMaxDev] = {};
+
+cudaMemPool_t get() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!tried[dev]) {
+    tried[dev] = true;
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    if (cudaMemPoolCreate(&p[dev], &props) == cudaSuccess) {
+      uint64_t keep = ~0ull;
+      cudaMemPoolSetAttribute(p[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+    } else {
+      cudaGetLastError();
+      p[dev] = nullptr;
+    }
+  }
+  return p[dev];
+}
+
+// bytes on stream s from the pool (in stream order) or from cudaMalloc
+cudaError_t alloc(void **ptr, size_t bytes, cudaStream_t s, bool *pooled) {
+  cudaMemPool_t mp = get();
+  *pooled = mp != nullptr;
+  return mp ? cudaMallocFromPoolAsync(ptr, bytes, mp, s) : cudaMalloc(ptr, bytes);
+}
+void release(void *ptr, bool pooled, cudaStream_t s) {
+  if (pooled)
+    cudaFreeAsync(ptr, s);
+  else
+    cudaFree(ptr);
+}
+}  // namespace pool
+
 struct EvPool {
   static constexpr int kCap = 96;
   cudaEvent_t a[kCap] = {}, b[kCap] = {};
@@ -38,6 +87,7 @@ struct feast_nh_ctx {
   CsrView A{}, AH{}, B{}, BH{};
   bool hasB = false;
   std::vector<void *> allocs;
+  std::vector<bool> pooled;  // allocs[i] came from the library's pool
   int kl = -1, ku = -1;     // band of (z B - A)
   int klp = 0, kup = 0;     // stored band widths (kl rounded up to even, kl+ku+1 even)
   void *bandT = nullptr;    // FP32: transposed factors for the conjugate-transpose solves
@@ -124,8 +174,10 @@ template <typename P>
 P *dalloc(feast_nh_ctx *ctx, size_t bytes) {
   void *p = nullptr;
   if (bytes == 0) bytes = 16;
-  CKC(cudaMalloc(&p, bytes));
+  bool pooled = false;
+  CKC(pool::alloc(&p, bytes, ctx->s, &pooled));
   ctx->allocs.push_back(p);
+  ctx->pooled.push_back(pooled);
   return reinterpret_cast<P *>(p);
 }
 
@@ -679,10 +731,18 @@ feast_nh_status feast_nh_nodes(const feast_nh_contour *c, double *z, double *w) 
   return FEAST_NH_OK;
 }
 
+feast_nh_status feast_nh_release_memory(void) {
+  std::lock_guard<std::mutex> lk(pool::mu);
+  for (int d = 0; d < pool::kMaxDev; ++d)
+    if (pool::p[d] && cudaMemPoolTrimTo(pool::p[d], 0) != cudaSuccess) return FEAST_NH_ECUDA;
+  return FEAST_NH_OK;
+}
+
 void feast_nh_destroy(feast_nh_ctx *ctx) {
   if (!ctx) return;
   if (ctx->s) cudaStreamSynchronize(ctx->s);
-  for (void *p : ctx->allocs) cudaFree(p);
+  for (size_t i = 0; i < ctx->allocs.size(); ++i) pool::release(ctx->allocs[i], ctx->pooled[i], ctx->s);
+  if (ctx->s) cudaStreamSynchronize(ctx->s);
   if (ctx->h_st) cudaFreeHost(ctx->h_st);
   if (ctx->h_small) cudaFreeHost(ctx->h_small);
   for (auto &e : ctx->ev)
@@ -1355,6 +1415,7 @@ struct feast_nh_batch {
   BatchStats *h_stats = nullptr;
   int *h_err = nullptr;
   std::vector<void *> allocs;
+  std::vector<bool> pooled;
   std::string err;
   cudaEvent_t ev[4] = {};
   std::vector<cudaEvent_t> ev_rr;
@@ -1390,8 +1451,10 @@ template <typename P>
 P *balloc(feast_nh_batch *b, size_t bytes) {
   void *p = nullptr;
   if (bytes == 0) bytes = 16;
-  BCK(cudaMalloc(&p, bytes));
+  bool pooled = false;
+  BCK(pool::alloc(&p, bytes, b->s, &pooled));
   b->allocs.push_back(p);
+  b->pooled.push_back(pooled);
   return reinterpret_cast<P *>(p);
 }
 
@@ -1538,7 +1601,8 @@ void batch_destroy_impl(feast_nh_batch *b) {
   if (!b) return;
   if (b->s) cudaStreamSynchronize(b->s);
   for (auto *c : b->ctx) feast_nh_destroy(c);
-  for (void *p : b->allocs) cudaFree(p);
+  for (size_t i = 0; i < b->allocs.size(); ++i) pool::release(b->allocs[i], b->pooled[i], b->s);
+  if (b->s) cudaStreamSynchronize(b->s);
   if (b->h_stats) cudaFreeHost(b->h_stats);
   if (b->h_err) cudaFreeHost(b->h_err);
   for (auto &e : b->ev)

@@ -77,7 +77,7 @@ EXPORTS = ["feast_nh_default_opts", "feast_nh_init", "feast_nh_filter", "feast_n
            "feast_nh_net_set_params", "feast_nh_net_get_params", "feast_nh_net_forward", "feast_nh_net_train_step",
            "feast_nh_net_destroy", "feast_nh_net_last_error", "feast_nh_set_network", "feast_nh_learned_pairs",
            "feast_nh_operator_loss", "feast_nh_net_backward", "feast_nh_gram",
-           "feast_nh_block_product"]
+           "feast_nh_block_product", "feast_nh_release_memory"]
 
 _lib = None
 
@@ -108,6 +108,8 @@ def lib():
     L.feast_nh_multishift_residual.argtypes = [vp, vp, vp, vp, vp, i32, i32]
     L.feast_nh_small_eig.argtypes = [vp, vp, i32, vp, vp]
     L.feast_nh_gram.argtypes = [vp, vp, vp, i32, i32, vp, i32]
+    L.feast_nh_release_memory.argtypes = []
+    L.feast_nh_release_memory.restype = i32
     L.feast_nh_block_product.argtypes = [vp, vp, vp, i32, i32, vp, i32]
     L.feast_nh_multishift_spmm.argtypes = [vp, vp, vp, i32, i32]
     L.feast_nh_inject_device_error.argtypes = [vp, C.c_uint32]
@@ -190,6 +192,14 @@ def contour_struct(con) -> tuple[ContourS, list]:
 def kernel_launches() -> int:
     """Kernels libfeast_nh.so has launched in this process."""
     return int(lib().feast_nh_kernel_launches())
+
+
+def release_memory():
+    """Give the library's reserved (unused) device workspace back to the
+    driver; contexts and batches reuse it otherwise."""
+    st = lib().feast_nh_release_memory()
+    if st != OK:
+        raise FeastError(st, "feast_nh_release_memory")
 
 
 def multishift_residual_noalloc(A_dev, B_dev, contour, X, BY, want_q=True, stream=None):
