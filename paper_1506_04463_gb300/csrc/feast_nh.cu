@@ -338,7 +338,8 @@ void factorize(feast_nh_ctx *ctx) {
 
 // Step 1 of Fig. alg:three on n x m blocks.  inner_tol: refinement target
 // (negative: opts.inner_tol).
-void do_filter(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, cxd *Q, cxd *Qh, int m, double inner_tol = -1.0) {
+void do_filter(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, cxd *Q, cxd *Qh, int m, double inner_tol = -1.0,
+               bool first_pass = false) {
   if (inner_tol < 0) inner_tol = ctx->o.inner_tol;
   if (!ctx->factored) factorize(ctx);
   const bool cs = cs_mode(ctx);
@@ -473,7 +474,16 @@ void do_filter(feast_nh_ctx *ctx, const cxd *Y, const cxd *Yh, cxd *Q, cxd *Qh, 
       g = launch_colnorm2(BhYh, m, m, n, ctx->colp, ctx->s);
       launch_reduce_parts(ctx->colp, g, m, ctx->bynorm2 + m, ctx->s);
     }
-    const int steps = ctx->o.inner_max < 1 ? 1 : ctx->o.inner_max;
+    // The loose first pass of a solve (inner tolerance >= 1e-2, FP32 factors)
+    // keeps its single solve unchecked: it only supplies the start subspace of
+    // the second iteration, whose refinement verifies the factors; its largest
+    // residual is recorded as NaN ("not measured")
+    const bool unchecked = first_pass && f32;
+    const int steps = unchecked ? 0 : (ctx->o.inner_max < 1 ? 1 : ctx->o.inner_max);
+    if (unchecked) {
+      CKC(cudaMemsetAsync(ctx->d_maxrel, 0xFF, sizeof(double), ctx->s));
+      ctx->inner_steps = 1;
+    }
     for (int it = 0; it < steps; ++it) {
       // residuals only: the node sum Q is formed once, from the final X
       int kr = ev_begin(ctx, ctx->ev_resid);
@@ -538,6 +548,7 @@ feast_nh_status status_from_err(feast_nh_ctx *ctx, int herr) {
 bool inner_missed(const feast_nh_ctx *ctx) {
   if (krylov(ctx)) return !ctx->krylov_ok;
   const double r = ctx->h_small[0];
+  if (std::isnan(r)) return false;  // the unchecked first pass
   return !(r <= ctx->last_inner_tol);
 }
 
@@ -1121,11 +1132,12 @@ feast_nh_status feast_nh_solve(feast_nh_ctx *ctx, const void *Y0, const void *Yh
       CKC(cudaEventRecord(ctx->ev[1], s));
       // The first iteration only supplies the start subspace of the second,
       // whose filter damps its errors by the convergence rate: its shifted
-      // systems need only the accuracy of the single-precision factors (a
-      // relative residual of 1e-2 stops the refinement), later iterations
-      // are refined to opts.inner_tol.
+      // systems need only the accuracy of the single-precision factors (one
+      // unchecked FP32 solve; with FP64 factors a relative residual of 1e-2
+      // stops the refinement), later iterations are refined to
+      // opts.inner_tol and verify the factors.
       const double tol_it = it == 1 ? std::fmax(ctx->o.inner_tol, 1e-2) : ctx->o.inner_tol;
-      do_filter(ctx, ctx->Yw, ctx->Yhw, ctx->Qw, ctx->Qhw, m, tol_it);
+      do_filter(ctx, ctx->Yw, ctx->Yhw, ctx->Qw, ctx->Qhw, m, tol_it, it == 1);
       CKC(cudaEventRecord(ctx->ev[2], s));
       mt = do_rr(ctx, ctx->Qw, ctx->Qhw, m, ctx->Yw, ctx->Yhw);
       CKC(cudaEventRecord(ctx->ev[3], s));
