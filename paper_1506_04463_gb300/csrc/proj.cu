@@ -34,6 +34,7 @@
 // Per-CTA partials are summed exactly in int64 by k_gram_tc_reduce, which
 // rounds once to FP64.  The result does not depend on the chunking.
 #include <algorithm>
+#include <atomic>
 #include "kernels.h"
 #include "tc.cuh"
 
@@ -335,6 +336,17 @@ __global__ void __launch_bounds__(256) k_gram_tc_reduce(const long long *__restr
 
 size_t gram_tc_smem_bytes() { return (size_t)2 * kBuf + 64; }
 
+// The dynamic shared-memory limit of kernel `which` raised once per device
+// (the attribute is per device).
+static void set_smem_attr(const void *func, size_t bytes, int which) {
+  static std::atomic<bool> done[2][64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || done[which][dev].load()) return;
+  cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  done[which][dev].store(true);
+}
+
 int gram_tc_chunks(int n, int mx, int my) {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
@@ -362,11 +374,7 @@ size_t gram_tc_part_max(int n) {
 // least gram_tc_part_bytes(nchunks, mx, my) bytes.
 void gram_tc(const cxd *X, int ldx, int mx, const cxd *Y, int ldy, int my, int n, cxd *G, long long *part,
              int nchunks, int *FXY, int *err, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_tc_smem_bytes());
-    attr = true;
-  }
+  set_smem_attr(reinterpret_cast<const void *>(k_gram_tc), gram_tc_smem_bytes(), 0);
   int *FX = FXY, *FY = FXY + kMaxM0;
   cudaMemsetAsync(FXY, 0, 2 * kMaxM0 * sizeof(int), s);
   const int erows = 1024;
@@ -568,11 +576,7 @@ size_t block_tc_smem_bytes() { return (size_t)2 * kBuf + 64 + (kMA + 32) * sizeo
 
 void block_tc(const cxd *X, int ldx, int mx, const cxd *S, int lds, int mz, int n, cxd *Z, int ldz, int *err,
               cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_block_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)block_tc_smem_bytes());
-    attr = true;
-  }
+  set_smem_attr(reinterpret_cast<const void *>(k_block_tc), block_tc_smem_bytes(), 1);
   const dim3 grid(ceil_div(n, kMA), ceil_div(mz, 32));
   k_block_tc<<<grid, kThreads, block_tc_smem_bytes(), s>>>(X, ldx, mx, S, lds, mz, n, Z, ldz, err);
   note_launch();
