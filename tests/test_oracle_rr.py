@@ -171,6 +171,21 @@ def test_complex_symmetric_16cube_family_vs_arpack():
     assert np.min(cosang) > 1 - 1e-9                          # x^_i parallel to conj(x_i)
 
 
+@pytest.mark.parametrize("seed", [7, 8])
+def test_random_sparse_family_vs_arpack(seed):
+    # the many-problem family (random sparse, 9 entries a row, shifted
+    # diagonal) at n < 1000 with its right-edge circle: the oracle finds every
+    # eigenvalue ARPACK finds inside, to 1e-10
+    bw = wl.config4(nprob=1, nmin=700, nmax=900, seed=seed, workers=1)
+    A = bw.A[0]
+    n = A.shape[0]
+    out = F.feast_nh(A, None, bw.contours[0], bw.m0, bw.Y0[:n], bw.Yh0[:n])
+    assert out["converged"] and out["m"] == bw.exact[0].size >= 16
+    assert _match(out["lam"], bw.exact[0]) < 1e-10
+    X, Xh = out["X"], out["Xh"]
+    assert np.max(np.abs(Xh.conj().T @ X - np.eye(out["m"]))) < 1e-10
+
+
 def test_resize_on_rank_deficient_start():
     # Duplicate start columns make B_Q singular: the subspace is resized
     # (eq. resize) and the run still converges.
